@@ -1,0 +1,258 @@
+/*
+ * qs.h — C ABI of the GB300 (sm_103a) state-vector engine for the QAOA /
+ * approximate-quantum-annealing (AQA) path of arXiv 2104.03293.
+ *
+ * The engine evolves an n-qubit state under the layered product of
+ * Eq. (QAOA_state),
+ *
+ *     |beta, gamma> = prod_{k=1}^{p} e^{-i beta_k H_D} e^{-i gamma_k H_C} |+>^n,
+ *
+ * with the mixer H_D = sum_i X_i (Sec. II.C.2) and the diagonal Ising cost
+ * H_C = sum_i h_i Z_i + sum_{i<j} J_ij Z_i Z_j (Eq. HC), and reads out
+ * <H_C> and the ground-state ("success") probability (Sec. III.A.1 and the
+ * success-probability definition of Sec. II.B.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Basis index z: qubit j is bit j of z, q_0 the least significant bit
+ *    (Sec. II.A, the rank-N tensor psi_{q_{N-1}...q_0}).  Z|0> = +|0>, so the
+ *    spin of qubit i in state z is s_i(z) = 1 - 2 bit_i(z).
+ *  - Within a layer the phase e^{-i gamma_k H_C} acts before the mixer
+ *    (Eq. QAOA_state; Appendix A writes the factors out).
+ *  - State layout in device memory: 2^n contiguous complex amplitudes,
+ *    interleaved (re, im): complex64 = 8 bytes (float2), complex128 = 16 bytes
+ *    (double2).  A caller-provided buffer must be 256-byte aligned.
+ *  - Every entry point returns a status (QS_OK on success).  On failure the
+ *    handle is left unchanged unless stated, and qs_last_error() returns a
+ *    thread-local, human-readable reason.  No entry point aborts the process.
+ *  - Host input arrays are copied before the call returns; the caller keeps
+ *    ownership.  Host output arrays are written only on success.
+ *  - Work is ordered on the handle's CUDA stream.  qs_evolve is asynchronous;
+ *    every call that returns host values synchronises that stream.
+ *  - Costs are exact integers: the weights h_i, J_ij must be integer
+ *    multiples of 2^-s for some s in 0..3 (half-integers arise in the exact-
+ *    cover mapping, Sec. II.B.3).  Internally costs are int32 in units of
+ *    2^-s; qs_cost_info reports s.  Other weights give QS_ENOTINT.
+ *
+ * Thread safety: distinct handles may be used from distinct host threads;
+ * one handle must not be used concurrently.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_state* qs_handle;
+typedef struct qs_batch* qs_batch_handle;
+
+enum qs_status {
+    QS_OK = 0,
+    QS_EINVAL = 1,    /* bad argument (size, index, pointer, non-finite angle)    */
+    QS_ENOMEM = 2,    /* device allocation failed or caller buffer too small      */
+    QS_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error)  */
+    QS_ETIMEOUT = 4,  /* a bounded device-side wait gave up (batched queue)       */
+    QS_ENOTINT = 5,   /* weights are not integer multiples of 2^-s, s <= 3        */
+    QS_ESTATE = 6     /* call out of order (e.g. evolve before set_ising)         */
+};
+
+enum qs_dtype { QS_C64 = 0, QS_C128 = 1 };
+enum qs_objective { QS_OBJ_ENERGY = 0, QS_OBJ_GROUND = 1 };
+enum qs_path { QS_PATH_TILED = 0, QS_PATH_PLAIN = 1 };
+
+/* Largest qubit count per dtype on one GPU. */
+#define QS_MAX_QUBITS_C64 34
+#define QS_MAX_QUBITS_C128 30
+/* Largest number of couplings accepted by qs_set_ising. */
+#define QS_MAX_EDGES 4096
+
+/* ------------------------------------------------------------------------ */
+/* Single state                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Create a handle for an n-qubit state (Sec. II.A: 2^n amplitudes).
+ *   n           1..34 (QS_C64) or 1..30 (QS_C128).
+ *   dtype       QS_C64 or QS_C128.
+ *   cuda_stream cudaStream_t to order all work on; NULL = the legacy default
+ *               stream.  The caller keeps it alive for the handle's lifetime.
+ *   device_buf  optional caller-owned device buffer for the state (for
+ *               example a torch tensor), >= 2^max(n, 12) * element bytes,
+ *               256-byte aligned.  NULL: the library allocates and frees it.
+ *               States with n < 12 are stored with 12 - n extra idle qubits
+ *               (no cost terms, left in |+>), which changes no readout.
+ *   buf_bytes   size of device_buf in bytes (ignored when it is NULL).
+ * Errors: QS_EINVAL (n, dtype, alignment), QS_ENOMEM (buffer too small or
+ * allocation failed), QS_ECUDA. */
+int qs_create(qs_handle* out, int n, int dtype, void* cuda_stream, void* device_buf, size_t buf_bytes);
+
+/* Release the handle and everything the library allocated for it.  A
+ * caller-provided buffer is not freed.  NULL is accepted. */
+int qs_destroy(qs_handle h);
+
+/* Select the kernel path: QS_PATH_TILED (default: multi-qubit HBM sweeps with
+ * the phase and readout fused) or QS_PATH_PLAIN (one launch per x-rotation
+ * and one per phase: the per-gate 2-component updates of
+ * Eq. twocomponentupdates; the reference point for the tiled path). */
+int qs_set_path(qs_handle h, int path);
+
+/* Set the Ising cost of Eq. (HC).
+ *   hfield   n doubles h_i.
+ *   n_edges  0..QS_MAX_EDGES couplings.
+ *   edges    2*n_edges int32 pairs (i, j), 0 <= i < j < n, no duplicates.
+ *   J        n_edges doubles J_ij.
+ * Validates, converts the weights to exact integers (see conventions), and
+ * runs the full-enumeration ground-state search (the t_FE search of
+ * Table III) on the device: minimum and maximum cost, lowest minimising index
+ * and the number of minimisers, all bit-exact.  Errors: QS_EINVAL, QS_ENOTINT
+ * (weights not on the 2^-s grid, or the cost range exceeds 2^24 units). */
+int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* edges, const double* J);
+
+/* Apply p layers of Eq. (QAOA_state).
+ *   gamma, beta  p host doubles each (finite).
+ *   from_plus    1: start from |+>^n (the ground state of H_I, Eq. HI);
+ *                0: continue from the current state.
+ * The readout (<H_C>, ground probability, norm) of the final state is fused
+ * into the last sweep and cached for qs_expect / qs_ground_prob.  p = 0 with
+ * from_plus = 1 prepares |+>^n.  Asynchronous.  Errors: QS_EINVAL,
+ * QS_ESTATE (no Ising cost set), QS_ECUDA. */
+int qs_evolve(qs_handle h, int p, const double* gamma, const double* beta, int from_plus);
+
+/* <H_C> of the current state, accumulated in FP64.  Synchronises. */
+int qs_expect(qs_handle h, double* E);
+
+/* Ground-state probability of the current state: total weight on every basis
+ * state of minimal cost (all minimisers, ties included).  Also returns the
+ * lowest minimising index, the minimal cost in units of 2^-s and the number
+ * of minimisers (any output pointer may be NULL).  Synchronises. */
+int qs_ground_prob(qs_handle h, double* P, int64_t* argmin, int64_t* cmin, int64_t* ground_count);
+
+/* E, P and sum |psi|^2 of the current state in one call.  Synchronises. */
+int qs_readout(qs_handle h, double* E, double* P, double* norm);
+
+/* Exact cost range and ground-state data of the Ising cost in units of 2^-s.
+ * Any output pointer may be NULL.  Synchronises. */
+int qs_cost_info(qs_handle h, int64_t* cmin, int64_t* cmax, int64_t* argmin, int64_t* ground_count,
+                 int* scale_shift);
+
+/* Gradient of F = <psi_p|O|psi_p> with respect to all 2p angles, where O is
+ * H_C (QS_OBJ_ENERGY) or the projector on the minimal-cost states
+ * (QS_OBJ_GROUND).  Not in the paper: reverse-mode through the unitary layers,
+ * which un-computes psi with the inverse layers (no checkpoints) while it
+ * propagates lambda = O psi_p and accumulates, per layer,
+ *   dF/dbeta_k  = 2 Im <lambda_k| H_D |psi_k>,
+ *   dF/dgamma_k = 2 Im <mu_k| H_C |phi_k>  (mu, phi: after undoing mixer k).
+ * Runs from |+>^n.  The reverse sweeps overwrite the state buffer (it ends
+ * near |+>^n), so call qs_evolve again to read psi_p.  Needs a second
+ * state-sized device buffer: set one with qs_set_adjoint_buffer, or the
+ * library allocates it on first use.  value, dgamma, dbeta: host outputs
+ * (value may be NULL).  Synchronises. */
+int qs_grad(qs_handle h, int p, const double* gamma, const double* beta, int objective,
+            double* value, double* dgamma, double* dbeta);
+
+/* Provide the adjoint state buffer used by qs_grad (caller-owned, same size
+ * and alignment rules as the state buffer).  NULL releases a library-owned
+ * one. */
+int qs_set_adjoint_buffer(qs_handle h, void* device_buf, size_t buf_bytes);
+
+/* Copy the state to host memory in the canonical basis order (bytes must be
+ * 2^n * element size).  For tests and small n.  Synchronises. */
+int qs_copy_state(qs_handle h, void* dst_host, size_t bytes);
+
+/* Device pointer of the state buffer.  The amplitudes stored there are
+ * psi_{z XOR F} where F is 0 or 2^n - 1 (*flip_all = 1); qs_canonicalize
+ * makes F = 0 in place.  Either output may be NULL. */
+int qs_state_ptr(qs_handle h, void** device_ptr, int* flip_all);
+
+/* Bring the stored amplitudes into the canonical basis order in place (one
+ * sweep when the stored frame is flipped, nothing otherwise).  Asynchronous. */
+int qs_canonicalize(qs_handle h);
+
+/* Sweeps per layer of the current plan (tiled path): the number of
+ * distinct tile shapes S and the HBM sweeps that p layers take. */
+int qs_plan_info(qs_handle h, int p, int* tile_shapes, int* sweeps);
+
+/* The same without a handle (host only, no GPU needed): an n-qubit state of
+ * the given dtype evolved from |+>^n through p layers. */
+int qs_plan_sweeps(int n, int dtype, int p, int* tile_shapes, int* sweeps);
+
+/* ------------------------------------------------------------------------ */
+/* Host-only helpers (no GPU needed)                                         */
+/* ------------------------------------------------------------------------ */
+
+/* First-order AQA angles on the linear schedule A(s) = 1 - s, B(s) = s:
+ *   gamma_k = tau * s_k,  beta_k = -tau * (1 - s_k).
+ * One first-order Trotter step of H(s) = A(s) H_I + B(s) H_C (Eqs. HI, Hofs)
+ * per knot; H_I = -H_D makes the driver factor e^{+i tau A H_D}, hence the
+ * negative beta (the sign of Eqs. beta_k - gamma_k).  s: p knots in [0, 1]. */
+int qs_aqa_angles(int p, double tau, const double* s, double* gamma, double* beta);
+
+/* The paper's second-order map, Eqs. (beta_k)-(gamma_k) with A = 1 - s,
+ * B = s:  beta_k = -tau (A(s_{k+1}) + A(s_k)) / 2 (k < p),
+ * beta_p = -tau A(s_p) / 2, gamma_k = tau B(s_k). */
+int qs_aqa_angles_2nd(int p, double tau, const double* s, double* gamma, double* beta);
+
+/* Chain rule for qs_aqa_angles: from dF/dgamma_k, dF/dbeta_k to
+ *   dF/dtau = sum_k [s_k dF/dgamma_k - (1 - s_k) dF/dbeta_k],
+ *   dF/ds_k = tau (dF/dgamma_k + dF/dbeta_k). */
+int qs_aqa_chain(int p, double tau, const double* s, const double* dgamma, const double* dbeta,
+                 double* dtau, double* ds);
+
+/* Thread-local text for the last non-OK status on this thread. */
+const char* qs_last_error(void);
+
+/* Library version string. */
+const char* qs_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Batched instances                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* A batch of `count` independent instances of possibly different n
+ * (1..QS_MAX_QUBITS_C64, complex64 only), all on one stream.  Their sweeps run
+ * together: each launch covers one sweep of every instance that still has
+ * work, so small states fill the GPU.  The library allocates every state.
+ * Errors: QS_EINVAL, QS_ENOMEM. */
+int qs_batch_create(qs_batch_handle* out, int count, const int* n, int dtype, void* cuda_stream);
+
+/* Ising cost of instance idx (same rules as qs_set_ising). */
+int qs_batch_set_ising(qs_batch_handle b, int idx, const double* hfield, int n_edges,
+                       const int32_t* edges, const double* J);
+
+/* Evolve every instance from |+> with its own p and angles.
+ *   p          count ints (0..QS_MAX_LAYERS_BATCH).
+ *   angle_off  count offsets into gamma/beta where instance i's p angles start.
+ *   gamma,beta host doubles.  Asynchronous. */
+int qs_batch_evolve(qs_batch_handle b, const int* p, const int64_t* angle_off, const double* gamma,
+                    const double* beta);
+
+/* E and P_ground per instance after qs_batch_evolve or qs_batch_grad
+ * (either pointer may be NULL).  Synchronises. */
+int qs_batch_results(qs_batch_handle b, double* E, double* P);
+
+/* Gradients of every instance at its current angles (the last evolve's).
+ * value (count), dgamma, dbeta (laid out like the angles).  Synchronises. */
+int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamma, double* dbeta);
+
+/* `steps` Adam steps minimising each instance's objective (QS_OBJ_ENERGY)
+ * over its 2p angles, entirely on the device: each step is a batched
+ * forward + adjoint and an Adam update (bias-corrected; lr, b1, b2, eps).
+ * gamma_io, beta_io hold the initial angles (laid out as in
+ * qs_batch_evolve's last call) and receive the final ones.  use_graph = 1
+ * captures one step in a CUDA graph and replays it.  Afterwards
+ * qs_batch_results gives E and P_ground at the final angles.  Synchronises. */
+int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2, double eps,
+                  double* gamma_io, double* beta_io, int use_graph);
+
+int qs_batch_destroy(qs_batch_handle b);
+
+#define QS_MAX_LAYERS_BATCH 64
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

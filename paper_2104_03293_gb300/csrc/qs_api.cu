@@ -1,0 +1,714 @@
+// C ABI of include/qs.h: single-state handles.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qs.h"
+#include "qs_api_common.h"
+
+namespace qs {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+    return set_error(QS_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// DevBuf / Uploader
+// ---------------------------------------------------------------------------
+int DevBuf::reserve(size_t bytes) {
+    if (bytes <= cap) return QS_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        cudaGetLastError();
+        return set_error(QS_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    cap = want;
+    return QS_OK;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+}
+
+Uploader::~Uploader() {
+    if (ev) cudaEventDestroy(ev);
+    if (host) cudaFreeHost(host);
+    dev.release();
+}
+
+int Uploader::upload(const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return QS_OK;
+    if (ev) {
+        cudaError_t e = cudaEventSynchronize(ev);
+        if (e != cudaSuccess) return cuda_error(e, "upload wait");
+    } else {
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
+    }
+    if (bytes > host_cap) {
+        if (host) cudaFreeHost(host);
+        host = nullptr;
+        host_cap = 0;
+        size_t want = bytes * 2;
+        cudaError_t e = cudaMallocHost(&host, want);
+        if (e != cudaSuccess) return set_error(QS_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+        host_cap = want;
+    }
+    if (bytes > dev.cap) {
+        // the device copy may still be read by queued work: drain first
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_error(e, "upload grow");
+    }
+    if (int rc = dev.reserve(bytes)) return rc;
+    std::memcpy(host, src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dev.ptr, host, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "upload");
+    e = cudaEventRecord(ev, st);
+    if (e != cudaSuccess) return cuda_error(e, "upload event");
+    return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Instance: validated Ising + device cost programs + ground-state data.
+// ---------------------------------------------------------------------------
+int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_edges, const int32_t* edges,
+                  const double* J, cudaStream_t st, DevBuf& enum_scratch) {
+    IsingInt I;
+    std::string err;
+    int rc = validate_ising(n_, hfield, n_edges, edges, J, I, err);
+    if (rc) return set_error(rc == 5 ? QS_ENOTINT : QS_EINVAL, "qs_set_ising: %s", err.c_str());
+    n = n_;
+    nphys = nphys_;
+    dtype = dtype_;
+    shift = I.shift;
+    // pad h to nphys qubits (idle qubits carry no terms)
+    std::vector<int32_t> h(nphys, 0);
+    for (int i = 0; i < n; ++i) h[i] = I.h[i];
+    std::vector<int32_t> blob;
+    auto add = [&](const std::vector<int32_t>& p) {
+        size_t off = blob.size();
+        blob.insert(blob.end(), p.begin(), p.end());
+        while (blob.size() % 4) blob.push_back(0);
+        return off;
+    };
+    for (int cfgi = 0; cfgi < 2; ++cfgi) {
+        const KernelCfg cfg = kernel_cfg(dtype, cfgi == 1);
+        shapes[cfgi] = make_shapes(nphys, cfg);
+        for (size_t s = 0; s < shapes[cfgi].size(); ++s)
+            for (int g = 0; g < kMaxLayouts; ++g) {
+                if (g >= num_layouts(shapes[cfgi][s].K, cfg.R)) { prog_off[cfgi][s][g] = prog_off[cfgi][s][0]; continue; }
+                int regq[6];
+                shape_regq(shapes[cfgi][s], cfg.R, g, regq);
+                prog_off[cfgi][s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, cfg.R));
+            }
+    }
+    {
+        int regq[6];
+        for (int b = 0; b < 6; ++b) regq[b] = b < n ? b : -1;
+        enum_off = add(build_cost_prog(n, I.h, I.ei, I.ej, I.J, regq, 6));
+    }
+    {
+        int regq[6] = {-1, -1, -1, -1, -1, -1};
+        std::vector<int32_t> pp = build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, 0);
+        plain_nf = pp[1];
+        plain_ne = pp[2];
+        plain_const0 = pp[3];
+        std::vector<int32_t> terms(pp.begin() + 12, pp.begin() + 12 + 2 * (plain_nf + plain_ne));
+        plain_off = add(terms.empty() ? std::vector<int32_t>{0, 0} : terms);
+    }
+    if (int r2 = progs.reserve(blob.size() * sizeof(int32_t))) return r2;
+    cudaError_t e = cudaMemcpyAsync(progs.ptr, blob.data(), blob.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_set_ising upload");
+    // ground-state search (bit exact) on the device
+    if (int r2 = enum_scratch.reserve(8 * 1024 * 4 * sizeof(int64_t) + 4 * sizeof(int64_t))) return r2;
+    int64_t* sc = reinterpret_cast<int64_t*>(enum_scratch.ptr);
+    e = launch_enumerate(prog(enum_off), n, sc + 4, 8 * 1024 * 4, sc, st);
+    if (e != cudaSuccess) return cuda_error(e, "enumerate launch");
+    int64_t res[4];
+    e = cudaMemcpyAsync(res, sc, sizeof res, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "enumerate");
+    cmin = res[0];
+    cmax = res[1];
+    argmin = res[2];
+    count = res[3];
+    // the phase table spans [cost_lo, cost_lo + range): the cost range of the
+    // padded state equals that of the n-qubit problem
+    cost_lo = (int)cmin;
+    range = (int)(cmax - cmin + 1);
+    if (range < 1) range = 1;
+    if (range > (1 << 22)) return set_error(QS_ENOTINT, "qs_set_ising: cost range %d exceeds the phase table limit", range);
+    valid = true;
+    return QS_OK;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+// ---------------------------------------------------------------------------
+// Single-state handle
+// ---------------------------------------------------------------------------
+struct qs_state {
+    int n = 0, nphys = 0, dtype = 0, path = QS_PATH_TILED;
+    size_t elem = 8;
+    cudaStream_t st = nullptr;
+    void* psi = nullptr;
+    bool own_psi = false;
+    void* lam = nullptr;
+    bool own_lam = false;
+    Instance inst;
+    DevBuf enum_scratch, layers_f, layers_r, tab_f, tab_r, partials, out, frame;
+    Uploader up, up_ang;
+    double theta_pad = 0.0;   // global phase of the idle padding qubits
+    bool have_readout = false;
+    int grid[2][2] = {{0, 0}, {0, 0}};  // [adjoint][K == K_A ? 0 : 1]
+    int device = 0;
+};
+
+static int check_handle(qs_handle h) {
+    if (!h) return set_error(QS_EINVAL, "NULL handle");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+    return QS_OK;
+}
+
+static int ensure_frame(qs_handle h) {
+    if (h->frame.ptr) return QS_OK;
+    if (int rc = h->frame.reserve(sizeof(int))) return rc;
+    cudaError_t e = cudaMemsetAsync(h->frame.ptr, 0, sizeof(int), h->st);
+    return e == cudaSuccess ? QS_OK : cuda_error(e, "frame init");
+}
+
+extern "C" {
+
+int qs_create(qs_handle* out, int n, int dtype, void* cuda_stream, void* device_buf, size_t buf_bytes) {
+    if (!out) return set_error(QS_EINVAL, "qs_create: out is NULL");
+    *out = nullptr;
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_create: bad dtype %d", dtype);
+    const int nmax = dtype == QS_C64 ? QS_MAX_QUBITS_C64 : QS_MAX_QUBITS_C128;
+    if (n < 1 || n > nmax) return set_error(QS_EINVAL, "qs_create: n = %d outside [1, %d]", n, nmax);
+    if (device_buf && (reinterpret_cast<uintptr_t>(device_buf) & 255))
+        return set_error(QS_EINVAL, "qs_create: device_buf must be 256-byte aligned");
+    std::unique_ptr<qs_state> h(new qs_state);
+    h->n = n;
+    h->nphys = n < kMinPhysQubits ? kMinPhysQubits : n;
+    h->dtype = dtype;
+    h->elem = dtype == QS_C64 ? 8 : 16;
+    h->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    const size_t need = ((size_t)1 << h->nphys) * h->elem;
+    if (device_buf) {
+        if (buf_bytes < need)
+            return set_error(QS_ENOMEM, "qs_create: device_buf holds %zu bytes, %zu needed", buf_bytes, need);
+        h->psi = device_buf;
+    } else {
+        e = cudaMalloc(&h->psi, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QS_ENOMEM, "qs_create: cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        }
+        h->own_psi = true;
+    }
+    if (int rc = ensure_frame(h.get())) {
+        if (h->own_psi) cudaFree(h->psi);
+        return rc;
+    }
+    *out = h.release();
+    return QS_OK;
+}
+
+int qs_destroy(qs_handle h) {
+    if (!h) return QS_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->st);
+    if (h->own_psi && h->psi) cudaFree(h->psi);
+    if (h->own_lam && h->lam) cudaFree(h->lam);
+    delete h;
+    return QS_OK;
+}
+
+int qs_set_path(qs_handle h, int path) {
+    if (int rc = check_handle(h)) return rc;
+    if (path != QS_PATH_TILED && path != QS_PATH_PLAIN) return set_error(QS_EINVAL, "qs_set_path: bad path");
+    h->path = path;
+    return QS_OK;
+}
+
+int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* edges, const double* J) {
+    if (int rc = check_handle(h)) return rc;
+    Instance tmp;
+    if (int rc = tmp.set(h->n, h->nphys, h->dtype, hfield, n_edges, edges, J, h->st, h->enum_scratch)) return rc;
+    h->inst = std::move(tmp);
+    h->have_readout = false;
+    return QS_OK;
+}
+
+}  // extern "C"
+
+// Grid size of the persistent sweep kernel for a tile shape.
+static int grid_for(qs_handle h, int K, int adjoint) {
+    const KernelCfg cfg = kernel_cfg(h->dtype, adjoint != 0);
+    int& g = h->grid[adjoint][K == cfg.K_A ? 0 : 1];
+    if (!g) g = sweep_grid(K, adjoint, h->dtype);
+    return g;
+}
+
+// Upload the angles and prepare forward (and optionally reverse) layers.
+static int prepare_layers(qs_handle h, int p, const double* gamma, const double* beta, bool from_plus, bool reverse,
+                          bool plain) {
+    Instance& I = h->inst;
+    std::vector<double> ang(2 * (size_t)(p > 0 ? p : 1), 0.0);
+    for (int k = 0; k < p; ++k) { ang[k] = gamma[k]; ang[p + k] = beta[k]; }
+    if (int rc = h->up_ang.upload(ang.data(), ang.size() * sizeof(double), h->st)) return rc;
+    cudaError_t e;
+    const double* dg = reinterpret_cast<const double*>(h->up_ang.dev.ptr);
+    const double* db = dg + p;
+    const size_t tsz = (size_t)(p > 0 ? p : 1) * I.range * h->elem * 2;
+    if (int rc = h->layers_f.reserve((size_t)(p + 1) * sizeof(LayerDev))) return rc;
+    if (int rc = h->tab_f.reserve(tsz)) return rc;
+    const int* f0 = from_plus ? nullptr : reinterpret_cast<const int*>(h->frame.ptr);
+    e = launch_prep(h->dtype, p, dg, db, h->nphys, I.cost_lo, I.range, I.shift, f0, plain ? 2 : 0,
+                    reinterpret_cast<LayerDev*>(h->layers_f.ptr), h->tab_f.ptr, I.range, h->st);
+    if (e != cudaSuccess) return cuda_error(e, "prep");
+    if (reverse) {
+        if (int rc = h->layers_r.reserve((size_t)(p + 1) * sizeof(LayerDev))) return rc;
+        if (int rc = h->tab_r.reserve(tsz)) return rc;
+        e = launch_prep(h->dtype, p, dg, db, h->nphys, I.cost_lo, I.range, I.shift, f0, 1,
+                        reinterpret_cast<LayerDev*>(h->layers_r.ptr), h->tab_r.ptr, I.range, h->st);
+        if (e != cudaSuccess) return cuda_error(e, "prep reverse");
+    }
+    return QS_OK;
+}
+
+static SweepTask make_task(qs_handle h, const Shape& sh, const PlanSweep& ps, int cfgi, int shape_idx, void* lam,
+                           const LayerDev* layers, const void* tab, int p, double* partials, int objective) {
+    Instance& I = h->inst;
+    SweepTask t;
+    std::memset(&t, 0, sizeof t);
+    t.psi = h->psi;
+    t.lam = lam;
+    t.layers = layers;
+    t.tab = tab;
+    for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_off[cfgi][shape_idx][g]);
+    t.partials = partials;
+    t.ntiles = sh.ntiles;
+    t.part_base = 0;
+    t.n = h->nphys;
+    t.c = sh.c;
+    t.g0 = sh.g0;
+    t.flags = ps.flags;
+    t.nrounds = ps.nr;
+    t.objective = objective;
+    t.tab_stride = I.range;
+    t.cost_lo = I.cost_lo;
+    t.gidx = (int)(I.cmin - I.cost_lo);
+    t.end_layer = p;
+    t.amp0 = std::pow(2.0, -0.5 * h->nphys);
+    t.np = (ps.flags & T_ADJOINT) ? 2 * ps.nr : ((ps.flags & T_READOUT) ? 3 : 0);
+    for (int r = 0; r < ps.nr; ++r) t.rounds[r] = ps.r[r];
+    return t;
+}
+
+// Blob uploaded once per call: tasks, per-launch tile prefixes, reduce tasks.
+struct CallBlob {
+    std::vector<unsigned char> bytes;
+    size_t add(const void* p, size_t n) {
+        size_t off = (bytes.size() + 15) & ~size_t(15);
+        bytes.resize(off + n);
+        std::memcpy(bytes.data() + off, p, n);
+        return off;
+    }
+};
+
+// Run a list of single-task sweeps; returns the byte offsets of each task.
+static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective, double* value,
+                     double* dgamma, double* dbeta) {
+    Instance& I = h->inst;
+    const KernelCfg cf = kernel_cfg(h->dtype, false);
+    const std::vector<Shape>& shf = I.shapes[0];
+    const std::vector<Shape>& sha = I.shapes[1];
+    std::vector<PlanSweep> fwd = plan_forward((int)shf.size(), p, from_plus);
+    std::vector<PlanSweep> rev;
+    if (mode_grad) {
+        fwd.back().flags |= T_WRITE_LAM;
+        rev = plan_reverse(fwd, sha, p);
+    }
+    // partial buffer
+    size_t part_need = 0;
+    for (auto& s : fwd) part_need = std::max(part_need, (size_t)shf[s.shape].ntiles * ((s.flags & T_READOUT) ? 3 : 0));
+    for (auto& s : rev) part_need = std::max(part_need, (size_t)sha[s.shape].ntiles * 2 * s.nr);
+    if (int rc = h->partials.reserve((part_need + 4) * sizeof(double))) return rc;
+    if (int rc = h->out.reserve((3 + 2 * (size_t)(p + 1)) * sizeof(double))) return rc;
+    double* dpart = reinterpret_cast<double*>(h->partials.ptr);
+    double* dout = reinterpret_cast<double*>(h->out.ptr);
+    // blob
+    CallBlob blob;
+    std::vector<size_t> fwd_off, rev_off, red_off;
+    std::vector<int> red_cnt;
+    const int64_t zero = 0;
+    size_t pre_off;
+    {
+        int64_t pre[2] = {0, 0};
+        pre_off = blob.add(pre, sizeof pre);  // placeholder; per-task prefixes added below
+        (void)zero;
+    }
+    std::vector<size_t> fwd_pre, rev_pre;
+    const LayerDev* lf = reinterpret_cast<const LayerDev*>(h->layers_f.ptr);
+    const LayerDev* lr = reinterpret_cast<const LayerDev*>(h->layers_r.ptr);
+    for (auto& s : fwd) {
+        SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective);
+        fwd_off.push_back(blob.add(&t, sizeof t));
+        int64_t pre[2] = {0, shf[s.shape].ntiles};
+        fwd_pre.push_back(blob.add(pre, sizeof pre));
+    }
+    for (auto& s : rev) {
+        SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective);
+        rev_off.push_back(blob.add(&t, sizeof t));
+        int64_t pre[2] = {0, sha[s.shape].ntiles};
+        rev_pre.push_back(blob.add(pre, sizeof pre));
+        // reduce tasks: beta partial -> out[3 + 2*layer], gamma -> out[3 + 2*layer + 1]
+        std::vector<ReduceTask> rts;
+        for (int r = 0; r < s.nr; ++r) {
+            const int L = s.r[r].layer;
+            rts.push_back(ReduceTask{dpart, sha[s.shape].ntiles, 2 * s.nr, 2 * r, 1, dout + 3 + 2 * L, 1, 1.0});
+            if (s.r[r].phase_post)
+                rts.push_back(ReduceTask{dpart, sha[s.shape].ntiles, 2 * s.nr, 2 * r + 1, 1, dout + 3 + 2 * L + 1, 1, 1.0});
+        }
+        red_off.push_back(rts.empty() ? 0 : blob.add(rts.data(), rts.size() * sizeof(ReduceTask)));
+        red_cnt.push_back((int)rts.size());
+    }
+    // final readout reduce
+    size_t rd_off;
+    {
+        const PlanSweep& last = fwd.back();
+        ReduceTask rt{dpart, shf[last.shape].ntiles, 3, 0, 3, dout, 0, 1.0};
+        rd_off = blob.add(&rt, sizeof rt);
+    }
+    if (int rc = h->up.upload(blob.bytes.data(), blob.bytes.size(), h->st)) return rc;
+    const unsigned char* dblob = reinterpret_cast<const unsigned char*>(h->up.dev.ptr);
+    (void)pre_off;
+    cudaError_t e;
+    if (mode_grad) {
+        e = cudaMemsetAsync(dout + 3, 0, 2 * (size_t)p * sizeof(double), h->st);
+        if (e != cudaSuccess) return cuda_error(e, "zero grads");
+    }
+    for (size_t i = 0; i < fwd.size(); ++i) {
+        const Shape& sh = shf[fwd[i].shape];
+        SweepLaunch L{sh.K, 0, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
+                      reinterpret_cast<const int64_t*>(dblob + fwd_pre[i])};
+        e = launch_sweep(L, grid_for(h, sh.K, 0), h->st);
+        if (e != cudaSuccess) return cuda_error(e, "sweep launch");
+    }
+    e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + rd_off), 1, h->st);
+    if (e != cudaSuccess) return cuda_error(e, "readout reduce");
+    for (size_t i = 0; i < rev.size(); ++i) {
+        const Shape& sh = sha[rev[i].shape];
+        SweepLaunch L{sh.K, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
+                      reinterpret_cast<const int64_t*>(dblob + rev_pre[i])};
+        e = launch_sweep(L, grid_for(h, sh.K, 1), h->st);
+        if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
+        if (red_cnt[i]) {
+            e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + red_off[i]), red_cnt[i], h->st);
+            if (e != cudaSuccess) return cuda_error(e, "adjoint reduce");
+        }
+    }
+    (void)cf;
+    (void)value; (void)dgamma; (void)dbeta;
+    return QS_OK;
+}
+
+static int run_plain(qs_handle h, int p, bool from_plus) {
+    Instance& I = h->inst;
+    cudaError_t e;
+    if (from_plus) {
+        e = launch_plain_init(h->dtype, h->psi, h->nphys, h->st);
+        if (e != cudaSuccess) return cuda_error(e, "plain init");
+    }
+    const LayerDev* lf = reinterpret_cast<const LayerDev*>(h->layers_f.ptr);
+    for (int k = 0; k < p; ++k) {
+        e = launch_plain_phase(h->dtype, h->psi, h->nphys, I.prog(I.plain_off), I.plain_nf, I.plain_ne,
+                               I.plain_const0, lf + k,
+                               reinterpret_cast<const unsigned char*>(h->tab_f.ptr) + (size_t)k * I.range * h->elem,
+                               I.cost_lo, I.range, h->st);
+        if (e != cudaSuccess) return cuda_error(e, "plain phase");
+        for (int q = 0; q < h->nphys; ++q) {
+            e = launch_plain_rx(h->dtype, h->psi, h->nphys, q, lf + k, h->st);
+            if (e != cudaSuccess) return cuda_error(e, "plain rx");
+        }
+    }
+    // readout
+    const int64_t nb = plain_readout_blocks(h->nphys);
+    if (int rc = h->partials.reserve((size_t)nb * 3 * sizeof(double) + 32)) return rc;
+    if (int rc = h->out.reserve(8 * sizeof(double))) return rc;
+    double* dpart = reinterpret_cast<double*>(h->partials.ptr);
+    e = launch_plain_readout(h->dtype, h->psi, h->nphys, I.prog(I.plain_off), I.plain_nf, I.plain_ne,
+                             I.plain_const0, (int)I.cmin, reinterpret_cast<const int*>(h->frame.ptr), dpart, nb,
+                             h->st);
+    if (e != cudaSuccess) return cuda_error(e, "plain readout");
+    ReduceTask rt{dpart, nb, 3, 0, 3, reinterpret_cast<double*>(h->out.ptr), 0, 1.0};
+    if (int rc = h->up.upload(&rt, sizeof rt, h->st)) return rc;
+    e = launch_reduce(reinterpret_cast<const ReduceTask*>(h->up.dev.ptr), 1, h->st);
+    if (e != cudaSuccess) return cuda_error(e, "plain reduce");
+    return QS_OK;
+}
+
+static int check_angles(int p, const double* gamma, const double* beta) {
+    if (p < 0 || p > QS_MAX_LAYERS_PREP) return set_error(QS_EINVAL, "p = %d outside [0, %d]", p, QS_MAX_LAYERS_PREP);
+    if (p > 0 && (!gamma || !beta)) return set_error(QS_EINVAL, "gamma or beta is NULL");
+    for (int k = 0; k < p; ++k)
+        if (!std::isfinite(gamma[k]) || !std::isfinite(beta[k])) return set_error(QS_EINVAL, "non-finite angle at layer %d", k);
+    return QS_OK;
+}
+
+extern "C" {
+
+int qs_evolve(qs_handle h, int p, const double* gamma, const double* beta, int from_plus) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->inst.valid) return set_error(QS_ESTATE, "qs_evolve: call qs_set_ising first");
+    if (int rc = check_angles(p, gamma, beta)) return rc;
+    const bool plain = h->path == QS_PATH_PLAIN;
+    if (int rc = prepare_layers(h, p, gamma, beta, from_plus != 0, false, plain)) return rc;
+    int rc = plain ? run_plain(h, p, from_plus != 0) : run_tiled(h, p, from_plus != 0, 0, 0, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    if (!plain) {
+        cudaError_t e = launch_set_frame(reinterpret_cast<int*>(h->frame.ptr),
+                                         reinterpret_cast<const LayerDev*>(h->layers_f.ptr), p, h->st);
+        if (e != cudaSuccess) return cuda_error(e, "set frame");
+    } else if (from_plus) {
+        cudaMemsetAsync(h->frame.ptr, 0, sizeof(int), h->st);
+    }
+    double bsum = 0;
+    for (int k = 0; k < p; ++k) bsum += beta[k];
+    h->theta_pad = (from_plus ? 0.0 : h->theta_pad) + (h->nphys - h->n) * bsum;
+    h->have_readout = true;
+    return QS_OK;
+}
+
+int qs_readout(qs_handle h, double* E, double* P, double* norm) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->have_readout) return set_error(QS_ESTATE, "no state evolved yet");
+    double r[3];
+    cudaError_t e = cudaMemcpyAsync(r, h->out.ptr, sizeof r, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_error(e, "readout");
+    const double sc = std::ldexp(1.0, -h->inst.shift);
+    if (E) *E = r[0] * sc;
+    if (P) *P = r[1];
+    if (norm) *norm = r[2];
+    return QS_OK;
+}
+
+int qs_expect(qs_handle h, double* E) { return qs_readout(h, E, nullptr, nullptr); }
+
+int qs_ground_prob(qs_handle h, double* P, int64_t* argmin, int64_t* cmin, int64_t* ground_count) {
+    if (int rc = qs_readout(h, nullptr, P, nullptr)) return rc;
+    if (argmin) *argmin = h->inst.argmin;
+    if (cmin) *cmin = h->inst.cmin;
+    if (ground_count) *ground_count = h->inst.count;
+    return QS_OK;
+}
+
+int qs_cost_info(qs_handle h, int64_t* cmin, int64_t* cmax, int64_t* argmin, int64_t* ground_count, int* scale_shift) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->inst.valid) return set_error(QS_ESTATE, "qs_cost_info: call qs_set_ising first");
+    if (cmin) *cmin = h->inst.cmin;
+    if (cmax) *cmax = h->inst.cmax;
+    if (argmin) *argmin = h->inst.argmin;
+    if (ground_count) *ground_count = h->inst.count;
+    if (scale_shift) *scale_shift = h->inst.shift;
+    return QS_OK;
+}
+
+int qs_set_adjoint_buffer(qs_handle h, void* device_buf, size_t buf_bytes) {
+    if (int rc = check_handle(h)) return rc;
+    const size_t need = ((size_t)1 << h->nphys) * h->elem;
+    if (device_buf && (reinterpret_cast<uintptr_t>(device_buf) & 255))
+        return set_error(QS_EINVAL, "adjoint buffer must be 256-byte aligned");
+    if (device_buf && buf_bytes < need)
+        return set_error(QS_ENOMEM, "adjoint buffer holds %zu bytes, %zu needed", buf_bytes, need);
+    cudaStreamSynchronize(h->st);
+    if (h->own_lam && h->lam) cudaFree(h->lam);
+    h->lam = device_buf;
+    h->own_lam = false;
+    return QS_OK;
+}
+
+int qs_grad(qs_handle h, int p, const double* gamma, const double* beta, int objective, double* value,
+            double* dgamma, double* dbeta) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->inst.valid) return set_error(QS_ESTATE, "qs_grad: call qs_set_ising first");
+    if (objective != QS_OBJ_ENERGY && objective != QS_OBJ_GROUND) return set_error(QS_EINVAL, "bad objective");
+    if (int rc = check_angles(p, gamma, beta)) return rc;
+    if (p > 0 && (!dgamma || !dbeta)) return set_error(QS_EINVAL, "dgamma or dbeta is NULL");
+    if (!h->lam) {
+        const size_t need = ((size_t)1 << h->nphys) * h->elem;
+        cudaError_t e = cudaMalloc(&h->lam, need);
+        if (e != cudaSuccess) {
+            h->lam = nullptr;
+            cudaGetLastError();
+            return set_error(QS_ENOMEM, "qs_grad: adjoint buffer cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        }
+        h->own_lam = true;
+    }
+    if (int rc = prepare_layers(h, p, gamma, beta, true, true, false)) return rc;
+    if (int rc = run_tiled(h, p, true, 1, objective, value, dgamma, dbeta)) return rc;
+    std::vector<double> r(3 + 2 * (size_t)p);
+    cudaError_t e = cudaMemcpyAsync(r.data(), h->out.ptr, r.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_grad");
+    const double sc = std::ldexp(1.0, -h->inst.shift);
+    const double lam_sc = objective == QS_OBJ_ENERGY ? sc : 1.0;
+    if (value) *value = objective == QS_OBJ_ENERGY ? r[0] * sc : r[1];
+    for (int k = 0; k < p; ++k) {
+        dbeta[k] = 2.0 * r[3 + 2 * k] * lam_sc;
+        dgamma[k] = 2.0 * r[3 + 2 * k + 1] * sc * lam_sc;
+    }
+    // the reverse pass un-computed the state: it no longer holds psi_p
+    h->have_readout = false;
+    cudaMemsetAsync(h->frame.ptr, 0, sizeof(int), h->st);
+    return QS_OK;
+}
+
+int qs_copy_state(qs_handle h, void* dst_host, size_t bytes) {
+    if (int rc = check_handle(h)) return rc;
+    const size_t need = ((size_t)1 << h->n) * h->elem;
+    if (!dst_host) return set_error(QS_EINVAL, "qs_copy_state: dst is NULL");
+    if (bytes != need) return set_error(QS_EINVAL, "qs_copy_state: %zu bytes given, %zu needed", bytes, need);
+    const size_t N = (size_t)1 << h->nphys;
+    std::vector<unsigned char> full(N * h->elem);
+    int frame = 0;
+    cudaError_t e = cudaMemcpyAsync(full.data(), h->psi, full.size(), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&frame, h->frame.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_copy_state");
+    const size_t fm = frame ? N - 1 : 0;
+    // n < nphys: the idle qubits are in |+> times the global phase e^{-i theta}
+    const double padscale = std::pow(2.0, 0.5 * (h->nphys - h->n));
+    const double cr = std::cos(h->theta_pad) * padscale, ci = std::sin(h->theta_pad) * padscale;
+    const size_t Nn = (size_t)1 << h->n;
+    for (size_t z = 0; z < Nn; ++z) {
+        const size_t src = z ^ fm;
+        if (h->dtype == QS_C64) {
+            const float* s = reinterpret_cast<const float*>(full.data()) + 2 * src;
+            float* d = reinterpret_cast<float*>(dst_host) + 2 * z;
+            const double re = s[0], im = s[1];
+            d[0] = (float)(re * cr - im * ci);
+            d[1] = (float)(re * ci + im * cr);
+        } else {
+            const double* s = reinterpret_cast<const double*>(full.data()) + 2 * src;
+            double* d = reinterpret_cast<double*>(dst_host) + 2 * z;
+            d[0] = s[0] * cr - s[1] * ci;
+            d[1] = s[0] * ci + s[1] * cr;
+        }
+    }
+    return QS_OK;
+}
+
+int qs_state_ptr(qs_handle h, void** device_ptr, int* flip_all) {
+    if (int rc = check_handle(h)) return rc;
+    if (device_ptr) *device_ptr = h->psi;
+    if (flip_all) {
+        int f = 0;
+        cudaError_t e = cudaMemcpyAsync(&f, h->frame.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return cuda_error(e, "qs_state_ptr");
+        *flip_all = f;
+    }
+    return QS_OK;
+}
+
+int qs_canonicalize(qs_handle h) {
+    int f = 0;
+    if (int rc = qs_state_ptr(h, nullptr, &f)) return rc;
+    if (!f) return QS_OK;
+    cudaError_t e = launch_flip_all(h->dtype, h->psi, h->nphys, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->frame.ptr, 0, sizeof(int), h->st);
+    return e == cudaSuccess ? QS_OK : cuda_error(e, "qs_canonicalize");
+}
+
+int qs_plan_info(qs_handle h, int p, int* tile_shapes, int* sweeps) {
+    if (!h) return set_error(QS_EINVAL, "NULL handle");
+    if (p < 0) return set_error(QS_EINVAL, "p < 0");
+    const auto sh = make_shapes(h->nphys, kernel_cfg(h->dtype, false));
+    if (tile_shapes) *tile_shapes = (int)sh.size();
+    if (sweeps) *sweeps = (int)plan_forward((int)sh.size(), p, true).size();
+    return QS_OK;
+}
+
+int qs_plan_sweeps(int n, int dtype, int p, int* tile_shapes, int* sweeps) {
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_plan_sweeps: bad dtype");
+    const int nmax = dtype == QS_C64 ? QS_MAX_QUBITS_C64 : QS_MAX_QUBITS_C128;
+    if (n < 1 || n > nmax || p < 0) return set_error(QS_EINVAL, "qs_plan_sweeps: bad n or p");
+    const int nphys = n < kMinPhysQubits ? kMinPhysQubits : n;
+    const auto sh = make_shapes(nphys, kernel_cfg(dtype, false));
+    if (tile_shapes) *tile_shapes = (int)sh.size();
+    if (sweeps) *sweeps = (int)plan_forward((int)sh.size(), p, true).size();
+    return QS_OK;
+}
+
+int qs_aqa_angles(int p, double tau, const double* s, double* gamma, double* beta) {
+    if (p < 0 || (p > 0 && (!s || !gamma || !beta)) || !std::isfinite(tau))
+        return set_error(QS_EINVAL, "qs_aqa_angles: bad arguments");
+    for (int k = 0; k < p; ++k) {
+        gamma[k] = tau * s[k];
+        beta[k] = -tau * (1.0 - s[k]);
+    }
+    return QS_OK;
+}
+
+int qs_aqa_angles_2nd(int p, double tau, const double* s, double* gamma, double* beta) {
+    if (p < 1 || !s || !gamma || !beta || !std::isfinite(tau))
+        return set_error(QS_EINVAL, "qs_aqa_angles_2nd: bad arguments");
+    for (int k = 0; k < p; ++k) {
+        const double A = 1.0 - s[k];
+        gamma[k] = tau * s[k];
+        beta[k] = (k + 1 < p) ? -tau * ((1.0 - s[k + 1]) + A) / 2.0 : -tau * A / 2.0;
+    }
+    return QS_OK;
+}
+
+int qs_aqa_chain(int p, double tau, const double* s, const double* dgamma, const double* dbeta, double* dtau,
+                 double* ds) {
+    if (p < 0 || (p > 0 && (!s || !dgamma || !dbeta || !ds)) || !dtau)
+        return set_error(QS_EINVAL, "qs_aqa_chain: bad arguments");
+    double t = 0;
+    for (int k = 0; k < p; ++k) {
+        t += s[k] * dgamma[k] - (1.0 - s[k]) * dbeta[k];
+        ds[k] = tau * (dgamma[k] + dbeta[k]);
+    }
+    *dtau = t;
+    return QS_OK;
+}
+
+const char* qs_last_error(void) { return g_last_error.c_str(); }
+
+const char* qs_version(void) { return "qs-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

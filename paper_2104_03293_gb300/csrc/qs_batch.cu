@@ -1,0 +1,532 @@
+// C ABI of include/qs.h: batched instances.
+//
+// Every instance keeps its own tile shapes and zig-zag sweep list.  Sweeps run
+// in waves: wave w is the w-th sweep of every instance that has one, issued as
+// at most one launch per tile size, each launch a list of tasks over which the
+// persistent CTAs stride.  Small states therefore share the GPU instead of
+// each leaving most SMs idle.  The whole optimiser step (preparation, forward
+// waves, reverse waves, reductions, Adam) has static launch parameters, so it
+// can be captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qs.h"
+#include "qs_api_common.h"
+
+using namespace qs;
+
+namespace {
+
+struct Launch {
+    int K, adjoint;
+    int ntasks;
+    int64_t total_tiles;
+    size_t task_off, pre_off;  // byte offsets in the uploaded blob
+};
+
+struct Wave {
+    std::vector<Launch> launches;
+    size_t red_off = 0;
+    int nred = 0;
+};
+
+struct Blob {
+    std::vector<unsigned char> b;
+    size_t add(const void* p, size_t n) {
+        size_t off = (b.size() + 15) & ~size_t(15);
+        b.resize(off + n);
+        if (n) std::memcpy(b.data() + off, p, n);
+        return off;
+    }
+};
+
+}  // namespace
+
+struct qs_batch {
+    int count = 0, dtype = 0, device = 0;
+    cudaStream_t st = nullptr;
+    std::vector<int> n, nphys;
+    std::vector<Instance> inst;
+    std::vector<size_t> st_off;  // element offsets of each state
+    DevBuf states, lams, enum_scratch;
+    // per-evolve data
+    std::vector<int> p;
+    std::vector<int64_t> aoff;
+    int64_t total = 0;
+    std::vector<double> host_angles;  // [gamma_all, beta_all]
+    DevBuf angles, grads, adam_m, adam_v, step;
+    DevBuf layers_f, layers_r, tab_f, tab_r, partials, out, frames;
+    std::vector<size_t> lay_off, tab_off;  // per instance: LayerDev index / table element offsets
+    Uploader up;
+    // plans (device blob in up.dev)
+    std::vector<Wave> fwd_waves, rev_waves;
+    size_t prep_f_off = 0, prep_r_off = 0;
+    bool plan_grad = false, planned = false;
+    int grid[2][2] = {{0, 0}, {0, 0}};
+    cudaGraphExec_t graph = nullptr;
+    bool have_results = false;
+    int objective = 0;
+};
+
+static int bgrid(qs_batch_handle b, int K, int adjoint) {
+    const KernelCfg cfg = kernel_cfg(b->dtype, adjoint != 0);
+    int& g = b->grid[adjoint][K == cfg.K_A ? 0 : 1];
+    if (!g) g = sweep_grid(K, adjoint, b->dtype);
+    return g;
+}
+
+static void drop_graph(qs_batch_handle b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+extern "C" {
+
+int qs_batch_create(qs_batch_handle* out, int count, const int* n, int dtype, void* cuda_stream) {
+    if (!out) return set_error(QS_EINVAL, "qs_batch_create: out is NULL");
+    *out = nullptr;
+    if (count < 1 || count > (1 << 20) || !n) return set_error(QS_EINVAL, "qs_batch_create: bad count or n");
+    if (dtype != QS_C64) return set_error(QS_EINVAL, "qs_batch_create: only QS_C64 batches are supported");
+    std::unique_ptr<qs_batch> b(new qs_batch);
+    b->count = count;
+    b->dtype = dtype;
+    b->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || n[i] > QS_MAX_QUBITS_C64) return set_error(QS_EINVAL, "qs_batch_create: n[%d] = %d", i, n[i]);
+        b->n.push_back(n[i]);
+        const int np = n[i] < kMinPhysQubits ? kMinPhysQubits : n[i];
+        b->nphys.push_back(np);
+        b->st_off.push_back(total);
+        total += (size_t)1 << np;  // 2^12 elements keep every state 256-byte aligned
+    }
+    if (int rc = b->states.reserve(total * 8)) return rc;
+    b->inst.resize(count);
+    *out = b.release();
+    return QS_OK;
+}
+
+int qs_batch_set_ising(qs_batch_handle b, int idx, const double* hfield, int n_edges, const int32_t* edges,
+                       const double* J) {
+    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (idx < 0 || idx >= b->count) return set_error(QS_EINVAL, "qs_batch_set_ising: idx %d out of range", idx);
+    cudaSetDevice(b->device);
+    Instance tmp;
+    if (int rc = tmp.set(b->n[idx], b->nphys[idx], b->dtype, hfield, n_edges, edges, J, b->st, b->enum_scratch))
+        return rc;
+    b->inst[idx] = std::move(tmp);
+    b->planned = false;
+    drop_graph(b);
+    return QS_OK;
+}
+
+}  // extern "C"
+
+// Build the wave plan and the layer / table buffers for the current p[].
+static int build_plan(qs_batch_handle b, bool grad, int objective) {
+    const int C = b->count;
+    // layer and table offsets
+    b->lay_off.assign(C, 0);
+    b->tab_off.assign(C, 0);
+    size_t lay = 0, tab = 0;
+    for (int i = 0; i < C; ++i) {
+        b->lay_off[i] = lay;
+        b->tab_off[i] = tab;
+        lay += (size_t)b->p[i] + 1;
+        tab += (size_t)std::max(b->p[i], 1) * b->inst[i].range;
+    }
+    if (int rc = b->layers_f.reserve(lay * sizeof(LayerDev))) return rc;
+    if (int rc = b->tab_f.reserve(tab * 8)) return rc;
+    if (grad) {
+        if (int rc = b->layers_r.reserve(lay * sizeof(LayerDev))) return rc;
+        if (int rc = b->tab_r.reserve(tab * 8)) return rc;
+    }
+    if (int rc = b->frames.reserve((size_t)C * sizeof(int))) return rc;
+    if (int rc = b->out.reserve((size_t)C * 3 * sizeof(double))) return rc;
+    if (int rc = b->grads.reserve((size_t)std::max<int64_t>(2 * b->total, 1) * sizeof(double))) return rc;
+    if (grad && !b->lams.ptr) {
+        if (int rc = b->lams.reserve(b->states.cap)) return rc;
+    }
+
+    std::vector<std::vector<PlanSweep>> fwd(C), rev(C);
+    size_t maxf = 0, maxr = 0;
+    for (int i = 0; i < C; ++i) {
+        fwd[i] = plan_forward((int)b->inst[i].shapes[0].size(), b->p[i], true);
+        if (grad) {
+            fwd[i].back().flags |= T_WRITE_LAM;
+            rev[i] = plan_reverse(fwd[i], b->inst[i].shapes[1], b->p[i]);
+        }
+        maxf = std::max(maxf, fwd[i].size());
+        maxr = std::max(maxr, rev[i].size());
+    }
+    const int K_A = kernel_cfg(b->dtype, false).K_A;
+    double* dout = reinterpret_cast<double*>(b->out.ptr);
+    double* dgr = reinterpret_cast<double*>(b->grads.ptr);
+    float2* states = reinterpret_cast<float2*>(b->states.ptr);
+    float2* lams = reinterpret_cast<float2*>(b->lams.ptr);
+    const LayerDev* lf = reinterpret_cast<const LayerDev*>(b->layers_f.ptr);
+    const LayerDev* lr = reinterpret_cast<const LayerDev*>(b->layers_r.ptr);
+    const float2* tf = reinterpret_cast<const float2*>(b->tab_f.ptr);
+    const float2* tr = reinterpret_cast<const float2*>(b->tab_r.ptr);
+
+    Blob blob;
+    size_t part_need = 0;
+    double* dpart = nullptr;  // patched below after sizing: tasks store offsets relative to it
+    // first pass: size partials per wave
+    auto wave_partials = [&](const std::vector<std::vector<PlanSweep>>& L, size_t w, int cfgi) {
+        size_t need = 0;
+        for (int i = 0; i < C; ++i) {
+            if (w >= L[i].size()) continue;
+            const PlanSweep& s = L[i][w];
+            const Shape& sh = b->inst[i].shapes[cfgi][s.shape];
+            const int np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
+            need += (size_t)sh.ntiles * np;
+        }
+        return need;
+    };
+    for (size_t w = 0; w < maxf; ++w) part_need = std::max(part_need, wave_partials(fwd, w, 0));
+    for (size_t w = 0; w < maxr; ++w) part_need = std::max(part_need, wave_partials(rev, w, 1));
+    if (int rc = b->partials.reserve((part_need + 4) * sizeof(double))) return rc;
+    dpart = reinterpret_cast<double*>(b->partials.ptr);
+
+    auto build_waves = [&](const std::vector<std::vector<PlanSweep>>& L, size_t nw, int adj, std::vector<Wave>& out) {
+        out.clear();
+        for (size_t w = 0; w < nw; ++w) {
+            Wave wave;
+            int64_t pbase = 0;
+            std::vector<ReduceTask> rts;
+            for (int kind = 0; kind < 2; ++kind) {
+                std::vector<SweepTask> tasks;
+                std::vector<int64_t> pre{0};
+                int K = 0;
+                for (int i = 0; i < C; ++i) {
+                    if (w >= L[i].size()) continue;
+                    const PlanSweep& s = L[i][w];
+                    const Instance& I = b->inst[i];
+                    const Shape& sh = I.shapes[adj][s.shape];
+                    if ((sh.K == K_A) != (kind == 0)) continue;
+                    K = sh.K;
+                    SweepTask t;
+                    std::memset(&t, 0, sizeof t);
+                    t.psi = states + b->st_off[i];
+                    t.lam = lams ? lams + b->st_off[i] : nullptr;
+                    t.layers = (adj ? lr : lf) + b->lay_off[i];
+                    t.tab = (adj ? tr : tf) + b->tab_off[i];
+                    for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_off[adj][s.shape][g]);
+                    t.partials = dpart;
+                    t.ntiles = sh.ntiles;
+                    t.part_base = 0;
+                    t.n = b->nphys[i];
+                    t.c = sh.c;
+                    t.g0 = sh.g0;
+                    t.flags = s.flags;
+                    t.nrounds = s.nr;
+                    t.objective = objective;
+                    t.tab_stride = I.range;
+                    t.cost_lo = I.cost_lo;
+                    t.gidx = (int)(I.cmin - I.cost_lo);
+                    t.end_layer = b->p[i];
+                    t.amp0 = std::pow(2.0, -0.5 * b->nphys[i]);
+                    t.np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
+                    for (int r = 0; r < s.nr; ++r) t.rounds[r] = s.r[r];
+                    // partial slots of this task: [pbase, pbase + ntiles) in units of np doubles
+                    const double* tp = dpart + pbase;
+                    if (t.np) {
+                        // store pointer shifted so that (part_base + tile) * np indexes this task's block
+                        t.partials = dpart + pbase;
+                    }
+                    const double sc = std::ldexp(1.0, -I.shift);
+                    if (s.flags & T_READOUT) {
+                        rts.push_back(ReduceTask{tp, sh.ntiles, 3, 0, 1, dout + 3 * i, 0, sc});
+                        rts.push_back(ReduceTask{tp, sh.ntiles, 3, 1, 2, dout + 3 * i + 1, 0, 1.0});
+                    }
+                    if (s.flags & T_ADJOINT) {
+                        const double lam_sc = objective == QS_OBJ_ENERGY ? sc : 1.0;
+                        for (int r = 0; r < s.nr; ++r) {
+                            const int Ly = s.r[r].layer;
+                            double* db = dgr + b->total + b->aoff[i] + Ly;
+                            double* dg = dgr + b->aoff[i] + Ly;
+                            rts.push_back(ReduceTask{tp, sh.ntiles, 2 * s.nr, 2 * r, 1, db, 1, 2.0 * lam_sc});
+                            if (s.r[r].phase_post)
+                                rts.push_back(ReduceTask{tp, sh.ntiles, 2 * s.nr, 2 * r + 1, 1, dg, 1, 2.0 * sc * lam_sc});
+                        }
+                    }
+                    pbase += (int64_t)sh.ntiles * t.np;
+                    tasks.push_back(t);
+                    pre.push_back(pre.back() + sh.ntiles);
+                }
+                if (tasks.empty()) continue;
+                Launch l;
+                l.K = K;
+                l.adjoint = adj;
+                l.ntasks = (int)tasks.size();
+                l.total_tiles = pre.back();
+                l.task_off = blob.add(tasks.data(), tasks.size() * sizeof(SweepTask));
+                l.pre_off = blob.add(pre.data(), pre.size() * sizeof(int64_t));
+                wave.launches.push_back(l);
+            }
+            wave.nred = (int)rts.size();
+            wave.red_off = rts.empty() ? 0 : blob.add(rts.data(), rts.size() * sizeof(ReduceTask));
+            out.push_back(wave);
+        }
+    };
+    build_waves(fwd, maxf, 0, b->fwd_waves);
+    build_waves(rev, maxr, 1, b->rev_waves);
+
+    // preparation tasks (angles live in b->angles: [gamma_all, beta_all])
+    const double* da = reinterpret_cast<const double*>(b->angles.ptr);
+    std::vector<PrepTask> pf, pr;
+    for (int i = 0; i < C; ++i) {
+        const Instance& I = b->inst[i];
+        PrepTask t{da + b->aoff[i], da + b->total + b->aoff[i], b->p[i], b->nphys[i], I.cost_lo, I.range, I.shift, 0,
+                   nullptr, const_cast<LayerDev*>(lf) + b->lay_off[i], const_cast<float2*>(tf) + b->tab_off[i], I.range};
+        pf.push_back(t);
+        t.reverse = 1;
+        t.layers = const_cast<LayerDev*>(lr) + b->lay_off[i];
+        t.tab = const_cast<float2*>(tr) + b->tab_off[i];
+        pr.push_back(t);
+    }
+    b->prep_f_off = blob.add(pf.data(), pf.size() * sizeof(PrepTask));
+    b->prep_r_off = grad ? blob.add(pr.data(), pr.size() * sizeof(PrepTask)) : 0;
+    if (int rc = b->up.upload(blob.b.data(), blob.b.size(), b->st)) return rc;
+    b->plan_grad = grad;
+    b->objective = objective;
+    b->planned = true;
+    drop_graph(b);
+    return QS_OK;
+}
+
+static int run_waves(qs_batch_handle b, const std::vector<Wave>& waves) {
+    const unsigned char* d = reinterpret_cast<const unsigned char*>(b->up.dev.ptr);
+    for (const Wave& w : waves) {
+        for (const Launch& l : w.launches) {
+            SweepLaunch L{l.K, l.adjoint, b->dtype, l.ntasks, l.total_tiles,
+                          reinterpret_cast<const SweepTask*>(d + l.task_off),
+                          reinterpret_cast<const int64_t*>(d + l.pre_off)};
+            cudaError_t e = launch_sweep(L, bgrid(b, l.K, l.adjoint), b->st);
+            if (e != cudaSuccess) return cuda_error(e, "batched sweep");
+        }
+        if (w.nred) {
+            cudaError_t e = launch_reduce(reinterpret_cast<const ReduceTask*>(d + w.red_off), w.nred, b->st);
+            if (e != cudaSuccess) return cuda_error(e, "batched reduce");
+        }
+    }
+    return QS_OK;
+}
+
+// One evaluation on the device angles: prep, forward waves (+ reverse waves).
+static int run_step(qs_batch_handle b, bool grad) {
+    const unsigned char* d = reinterpret_cast<const unsigned char*>(b->up.dev.ptr);
+    cudaError_t e = launch_prep_batch(b->dtype, reinterpret_cast<const PrepTask*>(d + b->prep_f_off), b->count, b->st);
+    if (e != cudaSuccess) return cuda_error(e, "batched prep");
+    if (grad) {
+        e = launch_prep_batch(b->dtype, reinterpret_cast<const PrepTask*>(d + b->prep_r_off), b->count, b->st);
+        if (e != cudaSuccess) return cuda_error(e, "batched prep reverse");
+        e = cudaMemsetAsync(b->grads.ptr, 0, (size_t)2 * b->total * sizeof(double), b->st);
+        if (e != cudaSuccess) return cuda_error(e, "zero grads");
+    }
+    if (int rc = run_waves(b, b->fwd_waves)) return rc;
+    if (grad)
+        if (int rc = run_waves(b, b->rev_waves)) return rc;
+    return QS_OK;
+}
+
+static int upload_angles(qs_batch_handle b) {
+    const size_t bytes = (size_t)std::max<int64_t>(2 * b->total, 1) * sizeof(double);
+    if (b->angles.cap < bytes) {
+        cudaStreamSynchronize(b->st);
+        if (int rc = b->angles.reserve(bytes)) return rc;
+        b->planned = false;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->angles.ptr, b->host_angles.data(), 2 * b->total * sizeof(double),
+                                    cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // pageable source
+    return e == cudaSuccess ? QS_OK : cuda_error(e, "angles upload");
+}
+
+extern "C" {
+
+int qs_batch_evolve(qs_batch_handle b, const int* p, const int64_t* angle_off, const double* gamma,
+                    const double* beta) {
+    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (!p || !angle_off || !gamma || !beta) return set_error(QS_EINVAL, "qs_batch_evolve: NULL argument");
+    cudaSetDevice(b->device);
+    for (int i = 0; i < b->count; ++i) {
+        if (!b->inst[i].valid) return set_error(QS_ESTATE, "instance %d has no Ising cost", i);
+        if (p[i] < 0 || p[i] > QS_MAX_LAYERS_BATCH) return set_error(QS_EINVAL, "p[%d] = %d out of range", i, p[i]);
+        if (angle_off[i] < 0) return set_error(QS_EINVAL, "angle_off[%d] < 0", i);
+        for (int k = 0; k < p[i]; ++k)
+            if (!std::isfinite(gamma[angle_off[i] + k]) || !std::isfinite(beta[angle_off[i] + k]))
+                return set_error(QS_EINVAL, "non-finite angle in instance %d", i);
+    }
+    // compact angle layout [gamma_all, beta_all]
+    bool same = (int)b->p.size() == b->count;
+    for (int i = 0; same && i < b->count; ++i) same = b->p[i] == p[i];
+    if (!same) {
+        b->p.assign(p, p + b->count);
+        b->aoff.assign(b->count, 0);
+        int64_t t = 0;
+        for (int i = 0; i < b->count; ++i) { b->aoff[i] = t; t += p[i]; }
+        b->total = t;
+        b->planned = false;
+    }
+    b->host_angles.assign(2 * (size_t)b->total, 0.0);
+    for (int i = 0; i < b->count; ++i)
+        for (int k = 0; k < p[i]; ++k) {
+            b->host_angles[b->aoff[i] + k] = gamma[angle_off[i] + k];
+            b->host_angles[b->total + b->aoff[i] + k] = beta[angle_off[i] + k];
+        }
+    if (int rc = upload_angles(b)) return rc;
+    if (!b->planned || b->plan_grad)
+        if (int rc = build_plan(b, false, 0)) return rc;
+    if (int rc = run_step(b, false)) return rc;
+    b->have_results = true;
+    return QS_OK;
+}
+
+int qs_batch_results(qs_batch_handle b, double* E, double* P) {
+    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (!b->have_results) return set_error(QS_ESTATE, "qs_batch_results: nothing evolved yet");
+    cudaSetDevice(b->device);
+    std::vector<double> r(3 * (size_t)b->count);
+    cudaError_t e = cudaMemcpyAsync(r.data(), b->out.ptr, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_batch_results");
+    for (int i = 0; i < b->count; ++i) {
+        if (E) E[i] = r[3 * i];
+        if (P) P[i] = r[3 * i + 1];
+    }
+    return QS_OK;
+}
+
+int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamma, double* dbeta) {
+    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if ((int)b->p.size() != b->count) return set_error(QS_ESTATE, "qs_batch_grad: call qs_batch_evolve first");
+    if (objective != QS_OBJ_ENERGY && objective != QS_OBJ_GROUND) return set_error(QS_EINVAL, "bad objective");
+    if (b->total > 0 && (!dgamma || !dbeta)) return set_error(QS_EINVAL, "dgamma or dbeta is NULL");
+    cudaSetDevice(b->device);
+    if (!b->planned || !b->plan_grad || b->objective != objective)
+        if (int rc = build_plan(b, true, objective)) return rc;
+    if (int rc = run_step(b, true)) return rc;
+    std::vector<double> g(2 * (size_t)b->total), r(3 * (size_t)b->count);
+    cudaError_t e = cudaMemcpyAsync(g.data(), b->grads.ptr, g.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.data(), b->out.ptr, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_batch_grad");
+    for (int i = 0; i < b->count; ++i) {
+        if (value) value[i] = objective == QS_OBJ_ENERGY ? r[3 * i] : r[3 * i + 1];
+        for (int k = 0; k < b->p[i]; ++k) {
+            dgamma[b->aoff[i] + k] = g[b->aoff[i] + k];
+            dbeta[b->aoff[i] + k] = g[b->total + b->aoff[i] + k];
+        }
+    }
+    b->have_results = true;
+    return QS_OK;
+}
+
+int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2, double eps, double* gamma_io,
+                  double* beta_io, int use_graph) {
+    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if ((int)b->p.size() != b->count) return set_error(QS_ESTATE, "qs_batch_adam: call qs_batch_evolve first");
+    if (steps < 0 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) || !(eps > 0))
+        return set_error(QS_EINVAL, "qs_batch_adam: bad hyper-parameters");
+    if (b->total > 0 && (!gamma_io || !beta_io)) return set_error(QS_EINVAL, "qs_batch_adam: NULL angles");
+    cudaSetDevice(b->device);
+    for (int i = 0; i < b->count; ++i)
+        for (int k = 0; k < b->p[i]; ++k) {
+            b->host_angles[b->aoff[i] + k] = gamma_io[b->aoff[i] + k];
+            b->host_angles[b->total + b->aoff[i] + k] = beta_io[b->aoff[i] + k];
+        }
+    if (int rc = upload_angles(b)) return rc;
+    if (!b->planned || !b->plan_grad || b->objective != QS_OBJ_ENERGY)
+        if (int rc = build_plan(b, true, QS_OBJ_ENERGY)) return rc;
+    const size_t nb = (size_t)std::max<int64_t>(2 * b->total, 1) * sizeof(double);
+    if (int rc = b->adam_m.reserve(nb)) return rc;
+    if (int rc = b->adam_v.reserve(nb)) return rc;
+    if (int rc = b->step.reserve(sizeof(int))) return rc;
+    cudaError_t e = cudaMemsetAsync(b->adam_m.ptr, 0, nb, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->adam_v.ptr, 0, nb, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->step.ptr, 0, sizeof(int), b->st);
+    if (e != cudaSuccess) return cuda_error(e, "adam init");
+    double* theta = reinterpret_cast<double*>(b->angles.ptr);
+    const double* grad = reinterpret_cast<const double*>(b->grads.ptr);
+    auto one_step = [&]() -> int {
+        if (int rc = run_step(b, true)) return rc;
+        cudaError_t e2 = launch_step_inc(reinterpret_cast<int*>(b->step.ptr), b->st);
+        if (e2 == cudaSuccess)
+            e2 = launch_adam(theta, grad, reinterpret_cast<double*>(b->adam_m.ptr), reinterpret_cast<double*>(b->adam_v.ptr),
+                             2 * b->total, reinterpret_cast<const int*>(b->step.ptr), lr, b1, b2, eps, b->st);
+        return e2 == cudaSuccess ? QS_OK : cuda_error(e2, "adam");
+    };
+    if (use_graph && steps > 0) {
+        // the graph bakes in lr, b1, b2, eps: capture a fresh one per call
+        drop_graph(b);
+        cudaGraph_t g = nullptr;
+        cudaStream_t cap = b->st;
+        bool own = false;
+        if (!cap) {  // the legacy stream cannot be captured
+            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_error(e, "capture stream");
+            own = true;
+            cudaStreamSynchronize(b->st);
+        }
+        cudaStream_t saved = b->st;
+        b->st = cap;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? one_step() : cuda_error(e, "begin capture");
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        b->st = saved;
+        if (rc == QS_OK && e2 != cudaSuccess) rc = cuda_error(e2, "end capture");
+        if (rc == QS_OK) {
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            if (e != cudaSuccess) rc = cuda_error(e, "graph instantiate");
+        }
+        if (g) cudaGraphDestroy(g);
+        for (int s = 0; rc == QS_OK && s < steps; ++s) {
+            e = cudaGraphLaunch(b->graph, cap);
+            if (e != cudaSuccess) rc = cuda_error(e, "graph launch");
+        }
+        if (own) {
+            cudaStreamSynchronize(cap);
+            cudaStreamDestroy(cap);
+            drop_graph(b);
+        }
+        if (rc) return rc;
+    } else {
+        for (int s = 0; s < steps; ++s)
+            if (int rc = one_step()) return rc;
+    }
+    // final readout at the optimised angles
+    if (int rc = run_step(b, false)) return rc;
+    std::vector<double> a(2 * (size_t)b->total);
+    e = cudaMemcpyAsync(a.data(), b->angles.ptr, a.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_batch_adam");
+    for (int i = 0; i < b->count; ++i)
+        for (int k = 0; k < b->p[i]; ++k) {
+            gamma_io[b->aoff[i] + k] = a[b->aoff[i] + k];
+            beta_io[b->aoff[i] + k] = a[b->total + b->aoff[i] + k];
+        }
+    b->host_angles = a;
+    b->have_results = true;
+    return QS_OK;
+}
+
+int qs_batch_destroy(qs_batch_handle b) {
+    if (!b) return QS_OK;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->st);
+    drop_graph(b);
+    delete b;
+    return QS_OK;
+}
+
+}  // extern "C"

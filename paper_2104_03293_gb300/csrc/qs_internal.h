@@ -1,0 +1,157 @@
+// Internal declarations shared by the host API and the kernels.
+// Nothing here is part of the public ABI (include/qs.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// Tiling constants.
+//
+// A sweep reads every amplitude once and writes it once.  The 2^n index bits
+// are split into "tile bits" (held on chip by one CTA) and the rest (which
+// tile).  A tile shape is: the c lowest index bits (carried, only there so
+// that each tile row is contiguous in HBM) plus a contiguous run of target
+// bits [g0, g0 + K - c) whose x-rotations the sweep applies.  The first shape
+// (shape A) has c = 0 and targets [0, K_A).
+// ---------------------------------------------------------------------------
+constexpr int kMinPhysQubits = 12;   // states with n < 12 are padded with idle qubits
+constexpr int kMaxRounds = 8;        // rounds (layers) fused into one sweep
+constexpr int kMaxShapes = 4;        // tile shapes per plan
+constexpr int kMaxLayouts = 3;       // register layouts per tile shape
+#define QS_MAX_LAYERS_PREP 1024          // layers per preparation call
+
+// Register-layout parameters per kernel configuration.
+struct KernelCfg {
+    int K_A;   // tile bits of shape A
+    int K_B;   // tile bits of shapes B, C, ...
+    int R;     // register bits per thread
+    int c_min; // carried low bits of shapes B, C, ... (row = 2^c elements)
+};
+KernelCfg kernel_cfg(int dtype, bool adjoint);
+
+// Flags of a sweep task.
+enum : int {
+    T_GEN = 1,        // generate |+> instead of loading (first forward sweep)
+    T_READOUT = 2,    // accumulate E, P, norm after the last round
+    T_WRITE_LAM = 4,  // write lambda = O psi (adjoint forward pass)
+    T_STORE = 8,      // write the tile back (clear only for the last reverse sweep)
+    T_ADJOINT = 16    // two arrays (psi, lambda), gradient accumulation
+};
+
+struct SweepRound {
+    int layer;       // index into the per-layer parameter array
+    int phase_pre;   // apply the layer's phase before the rotations
+    int phase_post;  // apply the layer's (inverse) phase after the rotations
+    int r0;          // targets of this layer rotated in earlier sweeps (adjoint scale)
+};
+
+// Per-layer device parameters, produced on the device from the angles.
+struct LayerDev {
+    double w;       // butterfly weight: a' = a + w (-i b), |w| <= 1 (float-exact for complex64)
+    double fabs;    // |f| = 1 / sqrt(1 + w^2): magnitude of the per-rotation scalar factor
+    float c, s;     // cos(beta), sin(beta) (plain path)
+    int frame;      // basis frame (0 / 1 = all bits flipped) when this layer's phase acts
+    int var;        // 1: cotangent form (flips the frame)
+};
+
+struct SweepTask {
+    void* psi;
+    void* lam;
+    const LayerDev* layers;
+    const void* tab;             // per-layer phase tables [layer][tab_stride] (Real2)
+    const int32_t* cprog[kMaxLayouts];
+    double* partials;            // per tile: np doubles
+    int64_t ntiles;
+    int64_t part_base;           // first partial slot of this task
+    int n, c, g0, flags;
+    int nrounds, objective;
+    int tab_stride, cost_lo;     // table index = cost - cost_lo
+    int gidx;                    // cmin - cost_lo (ground-state table index)
+    int end_layer;               // layers[end_layer].frame = frame after the last round
+    double amp0;                 // 2^{-n/2} for T_GEN
+    int np;                      // doubles per tile in partials
+    SweepRound rounds[kMaxRounds];
+};
+
+// A sweep over a list of tasks (one tile shape per launch).
+struct SweepLaunch {
+    int K;                 // tile bits (selects the kernel)
+    int adjoint;
+    int dtype;
+    int ntasks;
+    int64_t total_tiles;
+    const SweepTask* tasks;        // device
+    const int64_t* tile_prefix;    // device, ntasks + 1
+};
+
+// Cost program: the Ising cost of Eq. (HC) specialised to one register layout.
+// Built on the host (see build_cost_prog), evaluated per thread on the device.
+//   [0] R  [1] nf  [2] ne  [3] const0  [4..10) regq
+//   then nf pairs (i, h), ne pairs (i | j << 8, J),
+//   then for b < R: (fb0, cnt, cnt pairs (j, J)), then Q[2^R].
+std::vector<int32_t> build_cost_prog(int n, const std::vector<int32_t>& h, const std::vector<int32_t>& ei,
+                                     const std::vector<int32_t>& ej, const std::vector<int32_t>& J,
+                                     const int* regq, int R);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).  All return cudaError_t.
+// ---------------------------------------------------------------------------
+cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st);
+int sweep_grid(int K, int adjoint, int dtype);   // persistent grid size
+
+// Layer preparation: angles -> LayerDev + phase tables (forward or reverse).
+cudaError_t launch_prep(int dtype, int p, const double* gamma, const double* beta, int nphys,
+                        int cost_lo, int range, int shift, const int* frame0, int reverse,
+                        LayerDev* layers, void* tab, int tab_stride, cudaStream_t st);
+
+// Batched variant: one block per instance.
+struct PrepTask {
+    const double* gamma; const double* beta;
+    int p, nphys, cost_lo, range, shift, reverse;
+    const int* frame0;
+    LayerDev* layers; void* tab; int tab_stride;
+};
+cudaError_t launch_prep_batch(int dtype, const PrepTask* tasks, int ntasks, cudaStream_t st);
+
+// Reduce per-tile readout partials (E, P, norm) of one task into out[3].
+struct ReduceTask {
+    const double* partials;  // np doubles per tile
+    int64_t ntiles;
+    int np, off, count;      // reduce slots [off, off+count) of each tile
+    double* out;             // count doubles
+    int accumulate;          // add into out instead of overwriting
+    double mult;             // out (+)= mult * sum
+};
+cudaError_t launch_reduce(const ReduceTask* tasks, int ntasks, cudaStream_t st);
+
+// Full-enumeration ground-state search of a cost program with register bits
+// 0..5 over 2^n states: writes (cmin, cmax, argmin, count) as int64 into out.
+cudaError_t launch_enumerate(const int32_t* cprog, int n, int64_t* scratch, int64_t nscratch, int64_t* out,
+                             cudaStream_t st);
+
+// Plain (one launch per gate) kernels.
+cudaError_t launch_plain_init(int dtype, void* psi, int nphys, cudaStream_t st);
+cudaError_t launch_plain_phase(int dtype, void* psi, int nphys, const int32_t* terms, int nf, int ne, int const0,
+                               const LayerDev* layer, const void* tab, int cost_lo, int range, cudaStream_t st);
+cudaError_t launch_plain_rx(int dtype, void* psi, int nphys, int q, const LayerDev* layer, cudaStream_t st);
+cudaError_t launch_plain_readout(int dtype, const void* psi, int nphys, const int32_t* terms, int nf, int ne,
+                                 int const0, int cmin, const int* frame, double* partials, int64_t nblocks,
+                                 cudaStream_t st);
+int64_t plain_readout_blocks(int nphys);
+cudaError_t launch_flip_all(int dtype, void* psi, int nphys, cudaStream_t st);
+cudaError_t launch_set_frame(int* frame_dev, const LayerDev* layers, int p, cudaStream_t st);
+
+// Batched Adam on device angles.
+cudaError_t launch_adam(double* theta, const double* grad, double* m, double* v, int64_t count, const int* step,
+                        double lr, double b1, double b2, double eps, cudaStream_t st);
+cudaError_t launch_gather_grad(const double* dsrc, double* ddst, int64_t count, cudaStream_t st);
+cudaError_t launch_step_inc(int* step, cudaStream_t st);
+
+}  // namespace qs

@@ -1,0 +1,237 @@
+// Host-side planning: Ising validation and integer scaling, cost programs,
+// tile shapes and the zig-zag sweep schedule.  No CUDA calls here, so the
+// planner can be exercised on a machine without a GPU.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qs_plan.h"
+
+namespace qs {
+
+// Eq. (HC) restricted to one register layout.  For z = zt + (slot m placed on
+// the register qubits), with zt's register bits clear and spins s = 1 - 2 b:
+//   C(z) = C_out(zt) + sum_b fb_b(zt) s_b(m) + Q[m]
+// where C_out holds the terms without register qubits, fb_b the field on
+// register qubit b from h and the couplings to non-register qubits, and Q the
+// couplings among register qubits.
+std::vector<int32_t> build_cost_prog(int n, const std::vector<int32_t>& h, const std::vector<int32_t>& ei,
+                                     const std::vector<int32_t>& ej, const std::vector<int32_t>& J,
+                                     const int* regq, int R) {
+    std::vector<int> slot(n, -1);
+    for (int b = 0; b < R; ++b)
+        if (regq[b] >= 0 && regq[b] < n) slot[regq[b]] = b;
+    std::vector<int32_t> out(12, 0);
+    out[0] = R;
+    for (int b = 0; b < 6; ++b) out[5 + b] = (b < R) ? regq[b] : -1;
+    int64_t const0 = 0;
+    int nf = 0, ne = 0;
+    for (int i = 0; i < n; ++i) {
+        if (slot[i] >= 0 || (i < (int)h.size() ? h[i] : 0) == 0) continue;
+        out.push_back(i);
+        out.push_back(h[i]);
+        const0 += h[i];
+        ++nf;
+    }
+    const int m = (int)ei.size();
+    for (int e = 0; e < m; ++e) {
+        if (slot[ei[e]] >= 0 || slot[ej[e]] >= 0 || J[e] == 0) continue;
+        out.push_back(ei[e] | (ej[e] << 8));
+        out.push_back(J[e]);
+        const0 += J[e];
+        ++ne;
+    }
+    for (int b = 0; b < R; ++b) {
+        const int q = regq[b];
+        if (q < 0 || q >= n) {
+            out.push_back(0);
+            out.push_back(0);
+            continue;
+        }
+        int64_t fb0 = h[q];
+        std::vector<int32_t> lst;
+        for (int e = 0; e < m; ++e) {
+            int other = -1;
+            if (ei[e] == q && slot[ej[e]] < 0) other = ej[e];
+            else if (ej[e] == q && slot[ei[e]] < 0) other = ei[e];
+            if (other < 0 || J[e] == 0) continue;
+            fb0 += J[e];
+            lst.push_back(other);
+            lst.push_back(J[e]);
+        }
+        out.push_back((int32_t)fb0);
+        out.push_back((int32_t)(lst.size() / 2));
+        out.insert(out.end(), lst.begin(), lst.end());
+    }
+    const int qoff = (int)out.size();
+    for (int mm = 0; mm < (1 << R); ++mm) {
+        int64_t q = 0;
+        for (int e = 0; e < m; ++e) {
+            const int a = slot[ei[e]], b = slot[ej[e]];
+            if (a < 0 || b < 0) continue;
+            const int sa = ((mm >> a) & 1) ? -1 : 1, sb = ((mm >> b) & 1) ? -1 : 1;
+            q += (int64_t)J[e] * sa * sb;
+        }
+        out.push_back((int32_t)q);
+    }
+    out[1] = nf;
+    out[2] = ne;
+    out[3] = (int32_t)const0;
+    out[4] = qoff;
+    return out;
+}
+
+int validate_ising(int n, const double* hfield, int n_edges, const int32_t* edges, const double* J,
+                   IsingInt& out, std::string& err) {
+    if (n < 1 || n > 40) { err = "n out of range"; return 1; }
+    if (n_edges < 0 || n_edges > 4096) { err = "n_edges out of range [0, 4096]"; return 1; }
+    if (!hfield && n > 0) { err = "hfield is NULL"; return 1; }
+    if (n_edges > 0 && (!edges || !J)) { err = "edges or J is NULL"; return 1; }
+    std::vector<char> seen;
+    if (n <= 40) seen.assign((size_t)n * n, 0);
+    for (int e = 0; e < n_edges; ++e) {
+        const int i = edges[2 * e], j = edges[2 * e + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n) { err = "edge index out of range"; return 1; }
+        if (i >= j) { err = "edges must satisfy i < j"; return 1; }
+        if (seen[(size_t)i * n + j]) { err = "duplicate edge"; return 1; }
+        seen[(size_t)i * n + j] = 1;
+        if (!std::isfinite(J[e])) { err = "non-finite coupling"; return 1; }
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(hfield[i])) { err = "non-finite field"; return 1; }
+    // smallest s in 0..3 with every weight * 2^s an integer
+    int shift = -1;
+    for (int s = 0; s <= 3 && shift < 0; ++s) {
+        const double sc = std::ldexp(1.0, s);
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) ok = std::nearbyint(hfield[i] * sc) == hfield[i] * sc;
+        for (int e = 0; e < n_edges && ok; ++e) ok = std::nearbyint(J[e] * sc) == J[e] * sc;
+        if (ok) shift = s;
+    }
+    if (shift < 0) { err = "weights are not integer multiples of 2^-s for s <= 3"; return 5; }
+    const double sc = std::ldexp(1.0, shift);
+    out.n = n;
+    out.shift = shift;
+    out.h.assign(n, 0);
+    out.ei.clear(); out.ej.clear(); out.J.clear();
+    double bound = 0;
+    for (int i = 0; i < n; ++i) {
+        const double v = hfield[i] * sc;
+        bound += std::fabs(v);
+        if (std::fabs(v) > (double)(1 << 24)) { err = "field too large"; return 5; }
+        out.h[i] = (int32_t)v;
+    }
+    for (int e = 0; e < n_edges; ++e) {
+        const double v = J[e] * sc;
+        bound += std::fabs(v);
+        if (std::fabs(v) > (double)(1 << 24)) { err = "coupling too large"; return 5; }
+        out.ei.push_back(edges[2 * e]);
+        out.ej.push_back(edges[2 * e + 1]);
+        out.J.push_back((int32_t)v);
+    }
+    if (bound > (double)(1 << 24)) { err = "cost range exceeds 2^24 units"; return 5; }
+    out.bound = (int64_t)bound;
+    return 0;
+}
+
+std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg) {
+    std::vector<Shape> v;
+    Shape a;
+    a.K = cfg.K_A; a.c = 0; a.g0 = 0; a.nt = cfg.K_A;
+    a.ntiles = (int64_t)1 << (nphys - cfg.K_A);
+    v.push_back(a);
+    int g = cfg.K_A;
+    while (g < nphys) {
+        Shape s;
+        s.K = cfg.K_B;
+        s.nt = std::min(cfg.K_B - cfg.c_min, nphys - g);
+        s.c = cfg.K_B - s.nt;
+        s.g0 = g;
+        s.ntiles = (int64_t)1 << (nphys - cfg.K_B);
+        v.push_back(s);
+        g += s.nt;
+    }
+    return v;
+}
+
+void shape_regq(const Shape& s, int R, int g, int* regq) {
+    int lo = s.K - (g + 1) * R;
+    if (lo < 0) lo = 0;
+    for (int b = 0; b < 6; ++b) {
+        if (b >= R) { regq[b] = -1; continue; }
+        const int tb = lo + b;
+        regq[b] = tb < s.c ? tb : s.g0 + (tb - s.c);
+    }
+}
+
+int num_layouts(int K, int R) { return (K + R - 1) / R; }
+
+// Zig-zag schedule: layer k visits the shapes in order 0..S-1 (k even) or
+// S-1..0 (k odd).  The x-rotations of one layer commute, so the order inside a
+// layer is free; with it the last sweep of layer k and the first sweep of
+// layer k+1 share a shape and merge into one sweep, with the (diagonal) phase
+// of layer k+1 applied between the two rounds.
+std::vector<PlanSweep> plan_forward(int S, int p, bool gen) {
+    std::vector<PlanSweep> v;
+    for (int k = 0; k < p; ++k) {
+        for (int i = 0; i < S; ++i) {
+            const int s = (k % 2 == 0) ? i : (S - 1 - i);
+            const bool ph = (i == 0);
+            if (ph && !v.empty() && v.back().shape == s && v.back().nr < kMaxRounds) {
+                v.back().r[v.back().nr++] = SweepRound{k, 1, 0, 0};
+            } else {
+                PlanSweep w;
+                w.shape = s;
+                w.nr = 1;
+                w.r[0] = SweepRound{k, ph ? 1 : 0, 0, 0};
+                w.flags = T_STORE;
+                v.push_back(w);
+            }
+        }
+    }
+    if (v.empty()) {
+        PlanSweep w;
+        w.shape = 0;
+        w.nr = 0;
+        w.flags = T_STORE;
+        v.push_back(w);
+    }
+    if (gen) v.front().flags |= T_GEN;
+    v.back().flags |= T_READOUT;
+    return v;
+}
+
+// The adjoint schedule: the forward sweeps in reverse order, each with its
+// rounds reversed; a round undoes the layer's rotations, then its phase.
+std::vector<PlanSweep> plan_reverse(const std::vector<PlanSweep>& fwd, const std::vector<Shape>& shapes, int p) {
+    std::vector<PlanSweep> v;
+    std::vector<int> cnt(p > 0 ? p : 1, 0);
+    for (int i = (int)fwd.size() - 1; i >= 0; --i) {
+        const PlanSweep& f = fwd[i];
+        PlanSweep w;
+        w.shape = f.shape;
+        w.nr = f.nr;
+        w.flags = T_ADJOINT | T_STORE;
+        for (int r = 0; r < f.nr; ++r) {
+            const SweepRound& fr = f.r[f.nr - 1 - r];
+            w.r[r] = SweepRound{fr.layer, 0, fr.phase_pre, cnt[fr.layer]};
+            cnt[fr.layer] += shapes[f.shape].nt;
+        }
+        v.push_back(w);
+    }
+    if (!v.empty()) v.back().flags &= ~T_STORE;  // undoes the |+> generation: nothing to keep
+    return v;
+}
+
+int count_sweeps(int nphys, int dtype, int p) {
+    const KernelCfg cfg = kernel_cfg(dtype, false);
+    const auto sh = make_shapes(nphys, cfg);
+    return (int)plan_forward((int)sh.size(), p, true).size();
+}
+
+KernelCfg kernel_cfg(int dtype, bool adjoint) {
+    if (dtype == 0) return adjoint ? KernelCfg{12, 13, 5, 2} : KernelCfg{12, 13, 6, 2};
+    return adjoint ? KernelCfg{11, 12, 4, 2} : KernelCfg{11, 12, 5, 2};
+}
+
+}  // namespace qs

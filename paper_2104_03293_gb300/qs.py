@@ -1,0 +1,363 @@
+"""Python binding of the C ABI in include/qs.h (ctypes, marshalling only).
+
+Every numerical step runs in libqs.so.  PyTorch only supplies device memory
+(optional caller-owned state buffers) and the current CUDA stream.  If the
+library has not been built, or no CUDA device is present, the calls raise:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import INCLUDE, LIB
+
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_ENOTINT, QS_ESTATE = range(7)
+QS_C64, QS_C128 = 0, 1
+QS_OBJ_ENERGY, QS_OBJ_GROUND = 0, 1
+QS_PATH_TILED, QS_PATH_PLAIN = 0, 1
+MIN_PHYS_QUBITS = 12
+
+_STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_ENOTINT",
+           6: "QS_ESTATE"}
+
+
+class QSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_PI = ctypes.POINTER(ctypes.c_int)
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+
+_SIGS = {
+    "qs_create": [ctypes.POINTER(_P), _I, _I, _P, _P, ctypes.c_size_t],
+    "qs_destroy": [_P],
+    "qs_set_path": [_P, _I],
+    "qs_set_ising": [_P, _PD, _I, _PI32, _PD],
+    "qs_evolve": [_P, _I, _PD, _PD, _I],
+    "qs_expect": [_P, _PD],
+    "qs_ground_prob": [_P, _PD, _PI64, _PI64, _PI64],
+    "qs_readout": [_P, _PD, _PD, _PD],
+    "qs_cost_info": [_P, _PI64, _PI64, _PI64, _PI64, _PI],
+    "qs_grad": [_P, _I, _PD, _PD, _I, _PD, _PD, _PD],
+    "qs_set_adjoint_buffer": [_P, _P, ctypes.c_size_t],
+    "qs_copy_state": [_P, _P, ctypes.c_size_t],
+    "qs_state_ptr": [_P, ctypes.POINTER(_P), _PI],
+    "qs_canonicalize": [_P],
+    "qs_plan_info": [_P, _I, _PI, _PI],
+    "qs_plan_sweeps": [_I, _I, _I, _PI, _PI],
+    "qs_aqa_angles": [_I, _D, _PD, _PD, _PD],
+    "qs_aqa_angles_2nd": [_I, _D, _PD, _PD, _PD],
+    "qs_aqa_chain": [_I, _D, _PD, _PD, _PD, _PD, _PD],
+    "qs_last_error": [],
+    "qs_version": [],
+    "qs_batch_create": [ctypes.POINTER(_P), _I, _PI, _I, _P],
+    "qs_batch_set_ising": [_P, _I, _PD, _I, _PI32, _PD],
+    "qs_batch_evolve": [_P, _PI, _PI64, _PD, _PD],
+    "qs_batch_results": [_P, _PD, _PD],
+    "qs_batch_grad": [_P, _I, _PD, _PD, _PD],
+    "qs_batch_adam": [_P, _I, _D, _D, _D, _D, _PD, _PD, _I],
+    "qs_batch_destroy": [_P],
+}
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/qs.h."""
+    txt = open(os.path.join(INCLUDE, "qs.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(qs_\w+)\s*\(", txt, flags=re.M)))
+
+
+def lib():
+    """Load libqs.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_2104_03293_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("qs_last_error", "qs_version") else _I
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != QS_OK:
+        raise QSError(rc, lib().qs_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_PD)
+
+
+def _f64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream or None
+        except Exception:
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return getattr(stream, "cuda_stream", None) or None
+
+
+def phys_qubits(n: int) -> int:
+    return max(n, MIN_PHYS_QUBITS)
+
+
+class State:
+    """An n-qubit state on the GPU (qs_create / qs_destroy)."""
+
+    def __init__(self, n: int, dtype: str = "c64", stream=None, buffer=None):
+        self.n = int(n)
+        self.dtype = QS_C64 if dtype in ("c64", "complex64", QS_C64) else QS_C128
+        self.elem = 8 if self.dtype == QS_C64 else 16
+        self._buffer = buffer  # keep a caller tensor alive
+        self._adj = None
+        ptr, nbytes = None, 0
+        if buffer is not None:
+            ptr = buffer.data_ptr()
+            nbytes = buffer.numel() * buffer.element_size()
+        h = _P()
+        _check(lib().qs_create(ctypes.byref(h), self.n, self.dtype, _stream_ptr(stream), ptr, nbytes))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_path(self, path: int):
+        _check(lib().qs_set_path(self._h, int(path)))
+
+    def set_ising(self, h, edges, J):
+        h = _f64(h)
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        J = _f64(J)
+        _check(lib().qs_set_ising(self._h, _dptr(h), int(e.shape[0]), e.ctypes.data_as(_PI32), _dptr(J)))
+
+    def set_instance(self, inst):
+        self.set_ising(inst.h, inst.edges, inst.J)
+
+    def evolve(self, gamma, beta, from_plus: bool = True):
+        g, b = _f64(gamma), _f64(beta)
+        if g.shape != b.shape:
+            raise ValueError("gamma and beta differ in length")
+        _check(lib().qs_evolve(self._h, int(g.size), _dptr(g), _dptr(b), int(bool(from_plus))))
+
+    def readout(self):
+        E, P, N = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().qs_readout(self._h, ctypes.byref(E), ctypes.byref(P), ctypes.byref(N)))
+        return E.value, P.value, N.value
+
+    def expect(self) -> float:
+        E = ctypes.c_double()
+        _check(lib().qs_expect(self._h, ctypes.byref(E)))
+        return E.value
+
+    def ground_prob(self):
+        P = ctypes.c_double()
+        a, c, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().qs_ground_prob(self._h, ctypes.byref(P), ctypes.byref(a), ctypes.byref(c), ctypes.byref(k)))
+        return P.value, a.value, c.value, k.value
+
+    def cost_info(self):
+        vals = [ctypes.c_int64() for _ in range(4)]
+        s = ctypes.c_int()
+        _check(lib().qs_cost_info(self._h, *[ctypes.byref(v) for v in vals], ctypes.byref(s)))
+        return tuple(v.value for v in vals) + (s.value,)
+
+    def set_adjoint_buffer(self, buffer):
+        self._adj = buffer
+        ptr = None if buffer is None else buffer.data_ptr()
+        nbytes = 0 if buffer is None else buffer.numel() * buffer.element_size()
+        _check(lib().qs_set_adjoint_buffer(self._h, ptr, nbytes))
+
+    def grad(self, gamma, beta, objective: int = QS_OBJ_ENERGY):
+        g, b = _f64(gamma), _f64(beta)
+        dg, db = np.zeros_like(g), np.zeros_like(b)
+        v = ctypes.c_double()
+        _check(lib().qs_grad(self._h, int(g.size), _dptr(g), _dptr(b), int(objective), ctypes.byref(v), _dptr(dg),
+                             _dptr(db)))
+        return v.value, dg, db
+
+    def copy_state(self) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex64 if self.dtype == QS_C64 else np.complex128)
+        _check(lib().qs_copy_state(self._h, out.ctypes.data_as(_P), out.nbytes))
+        return out
+
+    def state_ptr(self):
+        p, f = _P(), ctypes.c_int()
+        _check(lib().qs_state_ptr(self._h, ctypes.byref(p), ctypes.byref(f)))
+        return p.value, f.value
+
+    def canonicalize(self):
+        _check(lib().qs_canonicalize(self._h))
+
+    def plan_info(self, p: int):
+        s, w = ctypes.c_int(), ctypes.c_int()
+        _check(lib().qs_plan_info(self._h, int(p), ctypes.byref(s), ctypes.byref(w)))
+        return s.value, w.value
+
+
+def plan_sweeps(n: int, p: int, dtype: int = QS_C64):
+    """(tile shapes, HBM sweeps for p layers) of the tiled path (host only)."""
+    s, w = ctypes.c_int(), ctypes.c_int()
+    _check(lib().qs_plan_sweeps(int(n), int(dtype), int(p), ctypes.byref(s), ctypes.byref(w)))
+    return s.value, w.value
+
+
+def aqa_angles(tau: float, s) -> tuple:
+    s = _f64(s)
+    g, b = np.zeros_like(s), np.zeros_like(s)
+    _check(lib().qs_aqa_angles(int(s.size), float(tau), _dptr(s), _dptr(g), _dptr(b)))
+    return g, b
+
+
+def aqa_angles_2nd(tau: float, s) -> tuple:
+    s = _f64(s)
+    g, b = np.zeros_like(s), np.zeros_like(s)
+    _check(lib().qs_aqa_angles_2nd(int(s.size), float(tau), _dptr(s), _dptr(g), _dptr(b)))
+    return g, b
+
+
+def aqa_chain(tau: float, s, dgamma, dbeta):
+    s, dg, db = _f64(s), _f64(dgamma), _f64(dbeta)
+    ds = np.zeros_like(s)
+    dt = ctypes.c_double()
+    _check(lib().qs_aqa_chain(int(s.size), float(tau), _dptr(s), _dptr(dg), _dptr(db), ctypes.byref(dt), _dptr(ds)))
+    return dt.value, ds
+
+
+def version() -> str:
+    return lib().qs_version().decode()
+
+
+class Batch:
+    """Independent instances evolved together (qs_batch_*)."""
+
+    def __init__(self, ns: Sequence[int], stream=None):
+        n = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+        self.count = int(n.size)
+        self.ns = n
+        h = _P()
+        _check(lib().qs_batch_create(ctypes.byref(h), self.count, n.ctypes.data_as(_PI), QS_C64, _stream_ptr(stream)))
+        self._h = h
+        self.p = None
+        self.off = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_ising(self, idx: int, h, edges, J):
+        h = _f64(h)
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        J = _f64(J)
+        _check(lib().qs_batch_set_ising(self._h, int(idx), _dptr(h), int(e.shape[0]), e.ctypes.data_as(_PI32),
+                                        _dptr(J)))
+
+    def _layout(self, gammas):
+        p = np.ascontiguousarray(np.asarray([len(g) for g in gammas], dtype=np.int32))
+        off = np.zeros(self.count, dtype=np.int64)
+        off[1:] = np.cumsum(p[:-1])
+        return p, off
+
+    def evolve(self, gammas, betas):
+        p, off = self._layout(gammas)
+        g = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in gammas]) if p.sum() else np.zeros(1))
+        b = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in betas]) if p.sum() else np.zeros(1))
+        self.p, self.off = p, off
+        _check(lib().qs_batch_evolve(self._h, p.ctypes.data_as(_PI), off.ctypes.data_as(_PI64), _dptr(g), _dptr(b)))
+
+    def results(self):
+        E, P = np.zeros(self.count), np.zeros(self.count)
+        _check(lib().qs_batch_results(self._h, _dptr(E), _dptr(P)))
+        return E, P
+
+    def _split(self, flat):
+        return [flat[o:o + k].copy() for o, k in zip(self.off, self.p)]
+
+    def grad(self, objective: int = QS_OBJ_ENERGY):
+        tot = int(self.p.sum())
+        v = np.zeros(self.count)
+        dg, db = np.zeros(max(tot, 1)), np.zeros(max(tot, 1))
+        _check(lib().qs_batch_grad(self._h, int(objective), _dptr(v), _dptr(dg), _dptr(db)))
+        return v, self._split(dg), self._split(db)
+
+    def adam(self, gammas, betas, steps: int, lr=0.01, b1=0.9, b2=0.999, eps=1e-8, use_graph: bool = True):
+        g = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in gammas]))
+        b = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in betas]))
+        _check(lib().qs_batch_adam(self._h, int(steps), lr, b1, b2, eps, _dptr(g), _dptr(b), int(bool(use_graph))))
+        return self._split(g), self._split(b)
+
+
+def _torch_energy_function():
+    import torch
+
+    class QSEnergy(torch.autograd.Function):
+        """F(gamma, beta) = <H_C> or P_ground of a State; backward uses qs_grad."""
+
+        @staticmethod
+        def forward(ctx, gamma, beta, state, objective=QS_OBJ_ENERGY):
+            g = gamma.detach().cpu().double().numpy()
+            b = beta.detach().cpu().double().numpy()
+            val, dg, db = state.grad(g, b, objective)
+            ctx.save_for_backward(torch.from_numpy(dg).to(gamma.dtype), torch.from_numpy(db).to(beta.dtype))
+            return torch.tensor(val, dtype=gamma.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dg, db = ctx.saved_tensors
+            return grad_out * dg, grad_out * db, None, None
+
+    return QSEnergy
+
+
+def energy(gamma, beta, state: State, objective: int = QS_OBJ_ENERGY):
+    """Differentiable objective through torch.autograd (gradients from qs_grad)."""
+    return _torch_energy_function().apply(gamma, beta, state, objective)

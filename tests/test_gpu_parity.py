@@ -1,0 +1,172 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (from the stated targets): state ||psi - psi_ref||_2 <= 1e-4 for
+complex64 (1e-10 for complex128); readout |E - E_ref| <= 1e-5 max(|E_ref|,
+sum|h| + sum|J|) and |P - P_ref| <= 1e-5; ground-state data bit-exact.
+Sizes span several tiles, every tile shape, ragged last shapes and the
+padded small-n case.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_03293_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2104_03293_gb300 import build, qs as _qs
+    build.build()
+    return _qs
+
+
+def e_tol(inst, E_ref):
+    return 1e-5 * max(abs(E_ref), float(np.abs(inst.h).sum() + np.abs(inst.J).sum()), 1.0)
+
+
+def run(qs, inst, g, b, dtype="c64", path=0):
+    st = qs.State(inst.n, dtype)
+    st.set_instance(inst)
+    if path:
+        st.set_path(path)
+    st.evolve(g, b)
+    return st
+
+
+def check_state(qs, inst, g, b, dtype="c64", path=0, tol=None):
+    st = run(qs, inst, g, b, dtype, path)
+    E, P, N = st.readout()
+    psi = st.copy_state().astype(np.complex128)
+    ref = oracle.evolve(inst, g, b)
+    Er, Pr, Nr = oracle.readout(inst, ref)
+    tol = tol if tol is not None else (1e-4 if dtype == "c64" else 1e-10)
+    err = np.linalg.norm(psi - ref)
+    assert err <= tol, (inst.name, err)
+    assert abs(E - Er) <= e_tol(inst, Er), (E, Er)
+    assert abs(P - Pr) <= 1e-5, (P, Pr)
+    assert abs(N - 1.0) <= 1e-5
+    st.close()
+    return err
+
+
+def test_config1_golden(qs):
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config1_maxcut3r_n12_p2.json")))
+    inst, g, b = I.config1()
+    for dtype in ("c128", "c64"):
+        st = run(qs, inst, g, b, dtype)
+        E, P, _ = st.readout()
+        Pg, arg, cmin, cnt = st.ground_prob()
+        assert (arg, cmin, cnt) == (rec["argmin"], rec["cmin"], rec["ground_count"])
+        tol = 1e-12 if dtype == "c128" else e_tol(inst, rec["E"])
+        assert abs(E - rec["E"]) <= tol and abs(P - rec["P_ground"]) <= (1e-12 if dtype == "c128" else 1e-5)
+    check_state(qs, inst, g, b, "c128")
+    check_state(qs, inst, g, b, "c64")
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 11, 12, 13, 14, 17, 20, 23, 24, 25])
+def test_state_parity_tiled(qs, n):
+    inst = I.erdos_renyi_ising(n, 1000 + n)
+    for p in (1, 2, 3, 5):
+        g, b = I.uniform_angles(p, 2000 + 10 * n + p)
+        check_state(qs, inst, g, b)
+
+
+@pytest.mark.parametrize("n", [3, 12, 13, 18, 24])
+def test_state_parity_c128(qs, n):
+    inst = I.erdos_renyi_ising(n, 3000 + n)
+    g, b = I.uniform_angles(3, 3100 + n)
+    check_state(qs, inst, g, b, "c128")
+
+
+@pytest.mark.parametrize("n", [4, 12, 16, 21])
+def test_state_parity_plain(qs, n):
+    inst = I.erdos_renyi_ising(n, 4000 + n)
+    g, b = I.uniform_angles(3, 4100 + n)
+    check_state(qs, inst, g, b, path=1)
+    check_state(qs, inst, g, b, "c128", path=1)
+
+
+def test_special_angles(qs):
+    inst = I.erdos_renyi_ising(15, 77)
+    cmin, _, _, cnt = oracle.ground(inst)
+    for g, b in [([0.0], [0.0]), ([0.7], [0.0]), ([0.0], [0.9]), ([0.4], [np.pi / 2]), ([1.1, 0.3], [np.pi / 4, -np.pi / 4]),
+                 ([0.2, 0.5, 0.9], [3 * np.pi / 4, np.pi, 2.0])]:
+        check_state(qs, inst, np.array(g), np.array(b))
+
+
+def test_p0_and_continuation(qs):
+    inst = I.erdos_renyi_ising(16, 5)
+    st = qs.State(16)
+    st.set_instance(inst)
+    st.evolve([], [])
+    psi = st.copy_state()
+    assert np.max(np.abs(psi - 2.0 ** -8)) <= 1e-7
+    g, b = I.uniform_angles(5, 6)
+    st.evolve(g[:2], b[:2])
+    st.evolve(g[2:], b[2:], from_plus=False)
+    ref = oracle.evolve(inst, g, b)
+    assert np.linalg.norm(st.copy_state() - ref) <= 1e-4
+    E, P, _ = st.readout()
+    Er, Pr, _ = oracle.readout(inst, ref)
+    assert abs(E - Er) <= e_tol(inst, Er) and abs(P - Pr) <= 1e-5
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (5, 2), (8, 3), (12, 4), (19, 5), (24, 6)])
+def test_ground_enumeration_bit_exact(qs, n, seed):
+    for inst in (I.erdos_renyi_ising(n, seed), I.maxcut_regular3(n, seed) if n % 2 == 0 and n >= 4 else None):
+        if inst is None:
+            continue
+        st = qs.State(n)
+        st.set_instance(inst)
+        cmin, cmax, arg, cnt, shift = st.cost_info()
+        rc = oracle.ground(inst)
+        assert shift == 0
+        assert (cmin, cmax, arg, cnt) == (int(rc[0]), int(rc[1]), rc[2], rc[3])
+
+
+def test_half_integer_weights(qs):
+    inst = I.erdos_renyi_ising(14, 9)
+    inst.h = inst.h * 0.5
+    inst.J = inst.J * 0.25
+    st = qs.State(14)
+    st.set_instance(inst)
+    cmin, cmax, arg, cnt, shift = st.cost_info()
+    rc = oracle.ground(inst)
+    assert shift == 2 and cmin == int(rc[0] * 4) and arg == rc[2] and cnt == rc[3]
+    g, b = I.uniform_angles(3, 10)
+    check_state(qs, inst, g, b)
+
+
+@pytest.mark.parametrize("objective", [0, 1])
+@pytest.mark.parametrize("n,p", [(5, 3), (12, 4), (14, 2), (17, 3), (24, 2)])
+def test_adjoint_matches_oracle(qs, objective, n, p):
+    inst = I.erdos_renyi_ising(n, 5000 + n)
+    g, b = I.uniform_angles(p, 5100 + n)
+    st = qs.State(n)
+    st.set_instance(inst)
+    v, dg, db = st.grad(g, b, objective)
+    vr, dgr, dbr = oracle.adjoint(inst, g, b, objective)
+    scale = max(1.0, float(np.max(np.abs(np.concatenate([dgr, dbr])))))
+    assert abs(v - vr) <= 1e-5 * max(1.0, abs(vr))
+    assert np.max(np.abs(dg - dgr)) <= 1e-4 * scale, (dg, dgr)
+    assert np.max(np.abs(db - dbr)) <= 1e-4 * scale, (db, dbr)
+
+
+def test_batched_matches_single(qs):
+    items = I.config2(count=12, n_lo=12, n_hi=20, p_hi=6)
+    bt = qs.Batch([inst.n for inst, _, _ in items])
+    for i, (inst, _, _) in enumerate(items):
+        bt.set_ising(i, inst.h, inst.edges, inst.J)
+    bt.evolve([g for _, g, _ in items], [b for _, _, b in items])
+    E, P = bt.results()
+    for i, (inst, g, b) in enumerate(items):
+        st = run(qs, inst, g, b)
+        Es, Ps, _ = st.readout()
+        assert E[i] == Es and P[i] == Ps  # same kernels, same per-tile order
+        Er, Pr = oracle.expect(inst, g, b)
+        assert abs(E[i] - Er) <= e_tol(inst, Er) and abs(P[i] - Pr) <= 1e-5
