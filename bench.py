@@ -1,0 +1,283 @@
+#!/usr/bin/env python3
+"""Benchmark of the QAOA / AQA state-vector path on GB300.
+
+One step = one pass of the whole hot path on the largest single-GPU workload:
+  A1  Ising cost set-up of a seeded ER(4) instance with h, J in U{-1,0,1}
+      (n = 34), including the full-enumeration ground-state search;
+  A6  first-order AQA angles, tau = 0.75, 20 linear knots s_k = k/21;
+  A2-A5  |+> -> 20 layers -> readout (<H_C>, ground probability), n = 34,
+      complex64 (137.4 GB state);
+  A7  adjoint gradient of the ground probability at n = 33 (two complex64
+      states in the same 137.4 GB buffer) and the chain rule to (tau, s_k).
+
+`value` is the forward throughput in amplitude-updates per second, summed
+over ranks: one layer applies n x-rotations and one diagonal phase to 2^n
+amplitudes, (n + 1) 2^n updates.  Inputs (instance, angles) come from host
+arrays every step; the state never leaves HBM.
+
+--impl reference times the CPU oracle (complex128, gate by gate) on the host
+cores on a bounded sample of the same workload family.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QAOA/AQA layer time & HBM GB/s at n=34; adjoint grad cost vs 4p FD forwards"
+UNIT = "amplitude-updates/s"
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(n: int = 22, layers: int = 1, seed_cfg: int = 5):
+    """Time the CPU oracle on one seeded ER(4) instance of the workload family:
+    `layers` gate-by-gate complex128 layers at n qubits.  Returns
+    (amplitude-updates/s, seconds, threads)."""
+    import numpy as np
+    import oracle
+    from paper_2104_03293_gb300 import instances as I
+    inst = I.erdos_renyi_ising(n, I.workload_seed(seed_cfg, 0), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    s = np.arange(1, layers + 1) / (layers + 1)
+    g, b = oracle.aqa_angles(0.75, s)
+    t0 = time.perf_counter()
+    psi = oracle.evolve(inst, g, b)
+    oracle.readout(inst, psi, cmin=0.0)
+    dt = time.perf_counter() - t0
+    return layers * (n + 1) * 2.0 ** n / dt, dt, oracle.num_threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_n, 1)
+    vals, secs = [], []
+    threads = 1
+    for _ in range(args.steps):
+        v, dt, threads = oracle_sample(args.ref_n, 1)
+        vals.append(v)
+        secs.append(dt)
+    value = sum(vals) / len(vals)
+    sample = (f"one gate-by-gate complex128 AQA layer at n={args.ref_n} (ER(4), h,J in U{{-1,0,1}}) per step; "
+              f"the n=34 state (275 GB in complex128) does not fit the host")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": "config 5a sample: AQA layer, ER(4) integer Ising",
+                                            "n": args.ref_n, "p": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=34)
+    ap.add_argument("--p", type=int, default=20)
+    ap.add_argument("--tau", type=float, default=0.75)
+    ap.add_argument("--grad-n", type=int, default=33)
+    ap.add_argument("--ref-n", type=int, default=22)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+    from paper_2104_03293_gb300 import build, instances as I, qs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    n, p, n2 = args.n, args.p, args.grad_n
+    inst, s, tau = I.config5(n=n, p=p, tau=args.tau)
+    inst2 = I.erdos_renyi_ising(n2, I.workload_seed(5, 1), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    N = 1 << n
+    buf = torch.empty(N, dtype=torch.complex64, device="cuda")
+    half = buf.view(torch.float32).view(2, -1).view(torch.complex64) if n2 == n - 1 else None
+    st = qs.State(n, "c64", buffer=buf)
+    if half is not None:
+        st2 = qs.State(n2, "c64", buffer=half[0])
+        st2.set_adjoint_buffer(half[1])
+    else:
+        st2 = qs.State(n2, "c64")
+    _, sweeps = qs.plan_sweeps(n, p)
+    _, sweeps2 = qs.plan_sweeps(n2, p)
+    stream = torch.cuda.current_stream()
+
+    def step(timing):
+        t0 = time.perf_counter()
+        st.set_ising(inst.h, inst.edges, inst.J)                       # A1 (H2D of h, edges, J)
+        g, b = qs.aqa_angles(tau, s)                                    # A6
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.evolve(g, b)                                                 # A2-A4 (+ fused readout)
+        e1.record(stream)
+        E, P, _ = st.readout()                                          # A5 (D2H)
+        t1 = time.perf_counter()
+        st2.set_ising(inst2.h, inst2.edges, inst2.J)
+        e2, e3, e4 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e2.record(stream)
+        st2.evolve(g, b)
+        e3.record(stream)
+        v, dg, db = st2.grad(g, b, qs.QS_OBJ_GROUND)                    # A7
+        e4.record(stream)
+        dtau, ds = qs.aqa_chain(tau, s, dg, db)
+        torch.cuda.synchronize()
+        if timing is not None:
+            timing["evolve_ms"].append(e0.elapsed_time(e1))
+            timing["fwd2_ms"].append(e2.elapsed_time(e3))
+            timing["grad_ms"].append(e3.elapsed_time(e4))
+            timing["e2e_s"].append(t1 - t0)
+        return E, P, v, dtau
+
+    for _ in range(args.warmup):
+        step(None)
+    timing = {"evolve_ms": [], "fwd2_ms": [], "grad_ms": [], "e2e_s": []}
+    clocks = ClockSampler(torch.cuda.current_device()).start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = qs.launch_count()
+    ta = torch.cuda.Event(enable_timing=True)
+    tb = torch.cuda.Event(enable_timing=True)
+    ta.record(stream)
+    for _ in range(args.steps):
+        E, P, v, dtau = step(timing)
+    tb.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = qs.launch_count() - l0
+    clk = clocks.stop()
+    total_ms = ta.elapsed_time(tb)
+    evolve_s = sum(timing["evolve_ms"]) / 1000.0
+    if dist:
+        t = torch.tensor([total_ms, evolve_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, evolve_s = float(t[0]), float(t[1])
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    updates = args.steps * p * (n + 1) * float(N)
+    value = world * updates / evolve_s
+    evolve_ms = statistics.mean(timing["evolve_ms"])
+    alg_bytes = (16.0 * sweeps - 8.0) * N          # first sweep only writes
+    achieved = alg_bytes / (evolve_ms / 1000.0) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    grad_fe = statistics.mean(timing["grad_ms"]) / statistics.mean(timing["fwd2_ms"])
+    e2e_s = statistics.mean(timing["e2e_s"])
+    h2d = inst.h.nbytes + inst.edges.nbytes + inst.J.nbytes + 2 * 8 * p
+    d2h = 3 * 8
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v_cpu, dt_cpu, thr = oracle_sample(args.ref_n, 1)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"one gate-by-gate complex128 AQA layer at n={args.ref_n} ({dt_cpu:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"config 5: AQA n={n} p={p} tau={tau} forward + readout; "
+                               f"grad of P_ground at n={n2} wrt tau and {p} knots",
+                   "n": n, "p": p, "grad_n": n2, "l2": "inputs larger than L2 (137 GB state)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "layer_ms": evolve_ms / p,
+        "sweeps_per_evolve": sweeps,
+        "grad_forward_equivalents": grad_fe,
+        "fd_forward_equivalents": 4 * p,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "sweep_kernel (average over the evolve's sweeps)",
+                     "peak_source": "measured" if peaks else "fallback"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": updates / args.steps / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "readout": {"E": E, "P_ground": P, "grad_P": v, "dP_dtau": dtau},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

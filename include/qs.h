@@ -179,6 +179,10 @@ int qs_plan_info(qs_handle h, int p, int* tile_shapes, int* sweeps);
  * the given dtype evolved from |+>^n through p layers. */
 int qs_plan_sweeps(int n, int dtype, int p, int* tile_shapes, int* sweeps);
 
+/* Number of kernels this library has launched in this process so far (all
+ * handles and batches).  For accounting in benchmarks. */
+int qs_launch_count(int64_t* count);
+
 /* ------------------------------------------------------------------------ */
 /* Host-only helpers (no GPU needed)                                         */
 /* ------------------------------------------------------------------------ */

@@ -707,6 +707,12 @@ int qs_aqa_chain(int p, double tau, const double* s, const double* dgamma, const
     return QS_OK;
 }
 
+int qs_launch_count(int64_t* count) {
+    if (!count) return set_error(QS_EINVAL, "qs_launch_count: NULL");
+    *count = launch_total();
+    return QS_OK;
+}
+
 const char* qs_last_error(void) { return g_last_error.c_str(); }
 
 const char* qs_version(void) { return "qs-gb300 0.1 (sm_103a)"; }

@@ -56,7 +56,7 @@ struct SweepRound {
 struct LayerDev {
     double w;       // butterfly weight: a' = a + w (-i b), |w| <= 1 (float-exact for complex64)
     double fabs;    // |f| = 1 / sqrt(1 + w^2): magnitude of the per-rotation scalar factor
-    float c, s;     // cos(beta), sin(beta) (plain path)
+    double c, s;    // cos(beta), sin(beta) (plain path)
     int frame;      // basis frame (0 / 1 = all bits flipped) when this layer's phase acts
     int var;        // 1: cotangent form (flips the frame)
 };
@@ -103,6 +103,10 @@ std::vector<int32_t> build_cost_prog(int n, const std::vector<int32_t>& h, const
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All return cudaError_t.
 // ---------------------------------------------------------------------------
+// Launch accounting (qs_launch_count): every launcher reports its kernels.
+cudaError_t note_launch(cudaError_t e, int kernels = 1);
+int64_t launch_total();
+
 cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st);
 int sweep_grid(int K, int adjoint, int dtype);   // persistent grid size
 

@@ -1,11 +1,22 @@
 // Support kernels: per-layer preparation from the angles, deterministic
 // reductions, the full-enumeration ground-state search, the plain per-gate
 // path, and the on-device Adam update.
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "qs_internal.h"
 
 namespace qs {
+
+static std::atomic<int64_t> g_launches{0};
+
+cudaError_t note_launch(cudaError_t e, int kernels) {
+    if (e == cudaSuccess) g_launches.fetch_add(kernels, std::memory_order_relaxed);
+    return e;
+}
+
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 template <class Real> struct R2;
 template <> struct R2<float> { using T = float2; };
@@ -50,8 +61,8 @@ __device__ void prep_layers(const double* gamma, const double* beta, int p, int 
             const double wq = (sizeof(Real) == 4) ? (double)(float)wd : wd;
             L.w = wq;
             L.fabs = 1.0 / sqrt(1.0 + wq * wq);
-            L.c = (float)c;
-            L.s = (float)s;
+            L.c = c;
+            L.s = s;
             L.frame = fr;
             // layer scalar f^n
             double mag = pow(L.fabs, (double)nphys), re, im;
@@ -115,14 +126,14 @@ cudaError_t launch_prep(int dtype, int p, const double* gamma, const double* bet
     else
         prep_kernel<double><<<1, 256, 0, st>>>(gamma, beta, p, nphys, cost_lo, range, shift, frame0, mode, layers,
                                               tab, tab_stride);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 cudaError_t launch_prep_batch(int dtype, const PrepTask* tasks, int ntasks, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
     if (dtype == 0) prep_batch_kernel<float><<<ntasks, 256, 0, st>>>(tasks);
     else prep_batch_kernel<double><<<ntasks, 256, 0, st>>>(tasks);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
@@ -152,7 +163,7 @@ __global__ void reduce_kernel(const ReduceTask* tasks) {
 cudaError_t launch_reduce(const ReduceTask* tasks, int ntasks, cudaStream_t st) {
     if (ntasks <= 0) return cudaSuccess;
     reduce_kernel<<<ntasks, 256, 0, st>>>(tasks);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +291,7 @@ cudaError_t launch_enumerate(const int32_t* cprog, int n, int64_t* scratch, int6
     enumerate_kernel<<<(int)blocks, 256, 0, st>>>(cprog, n, reinterpret_cast<long long*>(scratch));
     enumerate_final<<<1, 256, 0, st>>>(reinterpret_cast<long long*>(scratch), (int)blocks,
                                        reinterpret_cast<long long*>(out));
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError(), 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +392,7 @@ cudaError_t launch_plain_init(int dtype, void* psi, int nphys, cudaStream_t st) 
     const double a = pow(2.0, -0.5 * nphys);
     if (dtype == 0) plain_init_kernel<float><<<plain_grid(N), 256, 0, st>>>((float2*)psi, N, (float)a);
     else plain_init_kernel<double><<<plain_grid(N), 256, 0, st>>>((double2*)psi, N, a);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 cudaError_t launch_plain_phase(int dtype, void* psi, int nphys, const int32_t* terms, int nf, int ne, int const0,
@@ -393,14 +404,14 @@ cudaError_t launch_plain_phase(int dtype, void* psi, int nphys, const int32_t* t
     else
         plain_phase_kernel<double><<<plain_grid(N), 256, 0, st>>>((double2*)psi, N, terms, nf, ne, const0, layer,
                                                                   (const double2*)tab, cost_lo, range);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 cudaError_t launch_plain_rx(int dtype, void* psi, int nphys, int q, const LayerDev* layer, cudaStream_t st) {
     const uint64_t N = 1ull << nphys;
     if (dtype == 0) plain_rx_kernel<float><<<plain_grid(N / 2), 256, 0, st>>>((float2*)psi, N, q, layer);
     else plain_rx_kernel<double><<<plain_grid(N / 2), 256, 0, st>>>((double2*)psi, N, q, layer);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 cudaError_t launch_plain_readout(int dtype, const void* psi, int nphys, const int32_t* terms, int nf, int ne,
@@ -413,7 +424,7 @@ cudaError_t launch_plain_readout(int dtype, const void* psi, int nphys, const in
     else
         plain_readout_kernel<double><<<(int)nblocks, 256, 0, st>>>((const double2*)psi, N, terms, nf, ne, const0,
                                                                    cmin, frame, partials);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 // In-place reversal psi[z] <-> psi[~z]: brings a flipped frame back to the
@@ -433,14 +444,14 @@ cudaError_t launch_flip_all(int dtype, void* psi, int nphys, cudaStream_t st) {
     const uint64_t N = 1ull << nphys;
     if (dtype == 0) flip_kernel<float><<<plain_grid(N / 2), 256, 0, st>>>((float2*)psi, N);
     else flip_kernel<double><<<plain_grid(N / 2), 256, 0, st>>>((double2*)psi, N);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 __global__ void set_frame_kernel(int* frame, const LayerDev* layers, int p) { *frame = layers[p].frame; }
 
 cudaError_t launch_set_frame(int* frame_dev, const LayerDev* layers, int p, cudaStream_t st) {
     set_frame_kernel<<<1, 1, 0, st>>>(frame_dev, layers, p);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
@@ -465,14 +476,14 @@ cudaError_t launch_adam(double* theta, const double* grad, double* m, double* v,
     if (count <= 0) return cudaSuccess;
     int blocks = (int)((count + 255) / 256);
     adam_kernel<<<blocks, 256, 0, st>>>(theta, grad, m, v, count, step, lr, b1, b2, eps);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 __global__ void step_inc_kernel(int* step) { *step += 1; }
 
 cudaError_t launch_step_inc(int* step, cudaStream_t st) {
     step_inc_kernel<<<1, 1, 0, st>>>(step);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 __global__ void copy_kernel(const double* s, double* d, int64_t count) {
@@ -483,7 +494,7 @@ __global__ void copy_kernel(const double* s, double* d, int64_t count) {
 cudaError_t launch_gather_grad(const double* dsrc, double* ddst, int64_t count, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     copy_kernel<<<(int)((count + 255) / 256), 256, 0, st>>>(dsrc, ddst, count);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 }  // namespace qs

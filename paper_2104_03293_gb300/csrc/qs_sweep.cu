@@ -459,7 +459,7 @@ static cudaError_t launch_one(const SweepLaunch& L, int grid, cudaStream_t st) {
         attr_set = true;
     }
     kern<<<grid, 1 << (K - R), smem, st>>>(L.tasks, L.tile_prefix, L.ntasks, L.total_tiles);
-    return cudaGetLastError();
+    return note_launch(cudaGetLastError());
 }
 
 template <class Real, int K, int R, int NA>

@@ -64,6 +64,7 @@ _SIGS = {
     "qs_aqa_angles": [_I, _D, _PD, _PD, _PD],
     "qs_aqa_angles_2nd": [_I, _D, _PD, _PD, _PD],
     "qs_aqa_chain": [_I, _D, _PD, _PD, _PD, _PD, _PD],
+    "qs_launch_count": [_PI64],
     "qs_last_error": [],
     "qs_version": [],
     "qs_batch_create": [ctypes.POINTER(_P), _I, _PI, _I, _P],
@@ -268,6 +269,13 @@ def aqa_chain(tau: float, s, dgamma, dbeta):
 
 def version() -> str:
     return lib().qs_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by libqs.so in this process so far."""
+    c = ctypes.c_int64()
+    _check(lib().qs_launch_count(ctypes.byref(c)))
+    return c.value
 
 
 class Batch:
