@@ -179,6 +179,12 @@ int qs_plan_info(qs_handle h, int p, int* tile_shapes, int* sweeps);
  * the given dtype evolved from |+>^n through p layers. */
 int qs_plan_sweeps(int n, int dtype, int p, int* tile_shapes, int* sweeps);
 
+/* Tile shape k of the plan for an n-qubit state (host only): shape kind
+ * (0 contiguous, 1 strided), tile bits K, carried low bits c, and the two
+ * target runs [g0, g0 + n1) and [g1, g1 + K - c - n1).  Returns QS_EINVAL
+ * when k is past the last shape. */
+int qs_plan_shape(int n, int dtype, int k, int* kind, int* K, int* c, int* g0, int* n1, int* g1);
+
 /* Number of kernels this library has launched in this process so far (all
  * handles and batches).  For accounting in benchmarks. */
 int qs_launch_count(int64_t* count);

@@ -118,10 +118,10 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
     };
     for (int cfgi = 0; cfgi < 2; ++cfgi) {
         const KernelCfg cfg = kernel_cfg(dtype, cfgi == 1);
-        shapes[cfgi] = make_shapes(nphys, cfg);
+        shapes[cfgi] = make_shapes(nphys, cfg, page_bit_for(dtype));
         for (size_t s = 0; s < shapes[cfgi].size(); ++s)
             for (int g = 0; g < kMaxLayouts; ++g) {
-                if (g >= num_layouts(shapes[cfgi][s].K, cfg.R)) { prog_off[cfgi][s][g] = prog_off[cfgi][s][0]; continue; }
+                if (g >= num_layouts(shapes[cfgi][s], cfg.R)) { prog_off[cfgi][s][g] = prog_off[cfgi][s][0]; continue; }
                 int regq[6];
                 shape_regq(shapes[cfgi][s], cfg.R, g, regq);
                 prog_off[cfgi][s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, cfg.R));
@@ -183,7 +183,7 @@ struct qs_state {
     void* lam = nullptr;
     bool own_lam = false;
     Instance inst;
-    DevBuf enum_scratch, layers_f, layers_r, tab_f, tab_r, partials, out, frame;
+    DevBuf enum_scratch, layers_f, layers_r, tab_f, tab_r, partials, out, frame, err;
     Uploader up, up_ang;
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
@@ -201,8 +201,23 @@ static int check_handle(qs_handle h) {
 static int ensure_frame(qs_handle h) {
     if (h->frame.ptr) return QS_OK;
     if (int rc = h->frame.reserve(sizeof(int))) return rc;
+    if (int rc = h->err.reserve(sizeof(int))) return rc;
     cudaError_t e = cudaMemsetAsync(h->frame.ptr, 0, sizeof(int), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err.ptr, 0, sizeof(int), h->st);
     return e == cudaSuccess ? QS_OK : cuda_error(e, "frame init");
+}
+
+// After a synchronisation: report (and clear) a timed-out device wait.
+static int check_device_error(qs_handle h) {
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, h->err.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "error word");
+    if (v) {
+        cudaMemset(h->err.ptr, 0, sizeof(int));
+        h->have_readout = false;
+        return set_error(QS_ETIMEOUT, "a sweep kernel gave up waiting for a tile copy; the state is invalid");
+    }
+    return QS_OK;
 }
 
 extern "C" {
@@ -273,10 +288,9 @@ int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* 
 }  // extern "C"
 
 // Grid size of the persistent sweep kernel for a tile shape.
-static int grid_for(qs_handle h, int K, int adjoint) {
-    const KernelCfg cfg = kernel_cfg(h->dtype, adjoint != 0);
-    int& g = h->grid[adjoint][K == cfg.K_A ? 0 : 1];
-    if (!g) g = sweep_grid(K, adjoint, h->dtype);
+static int grid_for(qs_handle h, int kind, int adjoint) {
+    int& g = h->grid[adjoint][kind];
+    if (!g) g = sweep_grid(h->dtype, adjoint, kind);
     return g;
 }
 
@@ -308,7 +322,8 @@ static int prepare_layers(qs_handle h, int p, const double* gamma, const double*
 }
 
 static SweepTask make_task(qs_handle h, const Shape& sh, const PlanSweep& ps, int cfgi, int shape_idx, void* lam,
-                           const LayerDev* layers, const void* tab, int p, double* partials, int objective) {
+                           const LayerDev* layers, const void* tab, int p, double* partials, int objective,
+                           int* map_err) {
     Instance& I = h->inst;
     SweepTask t;
     std::memset(&t, 0, sizeof t);
@@ -333,25 +348,29 @@ static SweepTask make_task(qs_handle h, const Shape& sh, const PlanSweep& ps, in
     t.amp0 = std::pow(2.0, -0.5 * h->nphys);
     t.np = (ps.flags & T_ADJOINT) ? 2 * ps.nr : ((ps.flags & T_READOUT) ? 3 : 0);
     for (int r = 0; r < ps.nr; ++r) t.rounds[r] = ps.r[r];
+    t.kind = sh.kind;
+    t.n1 = sh.n1;
+    t.g1 = sh.g1;
+    (void)map_err;
     return t;
 }
 
 // Blob uploaded once per call: tasks, per-launch tile prefixes, reduce tasks.
+// 64-byte alignment keeps the tensor maps inside the tasks aligned.
 struct CallBlob {
     std::vector<unsigned char> bytes;
     size_t add(const void* p, size_t n) {
-        size_t off = (bytes.size() + 15) & ~size_t(15);
+        size_t off = (bytes.size() + 63) & ~size_t(63);
         bytes.resize(off + n);
         std::memcpy(bytes.data() + off, p, n);
         return off;
     }
 };
 
-// Run a list of single-task sweeps; returns the byte offsets of each task.
-static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective, double* value,
-                     double* dgamma, double* dbeta) {
+// Run the tiled schedule: forward sweeps (+ readout), and for a gradient the
+// reverse sweeps with their per-layer reductions.
+static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective) {
     Instance& I = h->inst;
-    const KernelCfg cf = kernel_cfg(h->dtype, false);
     const std::vector<Shape>& shf = I.shapes[0];
     const std::vector<Shape>& sha = I.shapes[1];
     std::vector<PlanSweep> fwd = plan_forward((int)shf.size(), p, from_plus);
@@ -360,7 +379,6 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         fwd.back().flags |= T_WRITE_LAM;
         rev = plan_reverse(fwd, sha, p);
     }
-    // partial buffer
     size_t part_need = 0;
     for (auto& s : fwd) part_need = std::max(part_need, (size_t)shf[s.shape].ntiles * ((s.flags & T_READOUT) ? 3 : 0));
     for (auto& s : rev) part_need = std::max(part_need, (size_t)sha[s.shape].ntiles * 2 * s.nr);
@@ -368,32 +386,24 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     if (int rc = h->out.reserve((3 + 2 * (size_t)(p + 1)) * sizeof(double))) return rc;
     double* dpart = reinterpret_cast<double*>(h->partials.ptr);
     double* dout = reinterpret_cast<double*>(h->out.ptr);
-    // blob
     CallBlob blob;
-    std::vector<size_t> fwd_off, rev_off, red_off;
+    std::vector<size_t> fwd_off, rev_off, fwd_pre, rev_pre, red_off;
     std::vector<int> red_cnt;
-    const int64_t zero = 0;
-    size_t pre_off;
-    {
-        int64_t pre[2] = {0, 0};
-        pre_off = blob.add(pre, sizeof pre);  // placeholder; per-task prefixes added below
-        (void)zero;
-    }
-    std::vector<size_t> fwd_pre, rev_pre;
     const LayerDev* lf = reinterpret_cast<const LayerDev*>(h->layers_f.ptr);
     const LayerDev* lr = reinterpret_cast<const LayerDev*>(h->layers_r.ptr);
+    int map_err = 0;
     for (auto& s : fwd) {
-        SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective);
+        SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective, &map_err);
         fwd_off.push_back(blob.add(&t, sizeof t));
-        int64_t pre[2] = {0, shf[s.shape].ntiles};
+        const int64_t pre[2] = {0, shf[s.shape].ntiles};
         fwd_pre.push_back(blob.add(pre, sizeof pre));
     }
     for (auto& s : rev) {
-        SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective);
+        SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective, &map_err);
         rev_off.push_back(blob.add(&t, sizeof t));
-        int64_t pre[2] = {0, sha[s.shape].ntiles};
+        const int64_t pre[2] = {0, sha[s.shape].ntiles};
         rev_pre.push_back(blob.add(pre, sizeof pre));
-        // reduce tasks: beta partial -> out[3 + 2*layer], gamma -> out[3 + 2*layer + 1]
+        // per round: beta partial -> out[3 + 2 layer], gamma partial -> out[3 + 2 layer + 1]
         std::vector<ReduceTask> rts;
         for (int r = 0; r < s.nr; ++r) {
             const int L = s.r[r].layer;
@@ -404,16 +414,11 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         red_off.push_back(rts.empty() ? 0 : blob.add(rts.data(), rts.size() * sizeof(ReduceTask)));
         red_cnt.push_back((int)rts.size());
     }
-    // final readout reduce
-    size_t rd_off;
-    {
-        const PlanSweep& last = fwd.back();
-        ReduceTask rt{dpart, shf[last.shape].ntiles, 3, 0, 3, dout, 0, 1.0};
-        rd_off = blob.add(&rt, sizeof rt);
-    }
+    const ReduceTask rt{dpart, shf[fwd.back().shape].ntiles, 3, 0, 3, dout, 0, 1.0};
+    const size_t rd_off = blob.add(&rt, sizeof rt);
     if (int rc = h->up.upload(blob.bytes.data(), blob.bytes.size(), h->st)) return rc;
     const unsigned char* dblob = reinterpret_cast<const unsigned char*>(h->up.dev.ptr);
-    (void)pre_off;
+    int* derr = reinterpret_cast<int*>(h->err.ptr);
     cudaError_t e;
     if (mode_grad) {
         e = cudaMemsetAsync(dout + 3, 0, 2 * (size_t)p * sizeof(double), h->st);
@@ -421,26 +426,25 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     }
     for (size_t i = 0; i < fwd.size(); ++i) {
         const Shape& sh = shf[fwd[i].shape];
-        SweepLaunch L{sh.K, 0, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
-                      reinterpret_cast<const int64_t*>(dblob + fwd_pre[i])};
-        e = launch_sweep(L, grid_for(h, sh.K, 0), h->st);
+        SweepLaunch L{sh.kind, sweep_variant(fwd[i].flags, fwd[i].nr, fwd[i].r), 0, h->dtype, 1, sh.ntiles,
+                      reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
+                      reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
+        e = launch_sweep(L, grid_for(h, sh.kind, 0), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
     }
     e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + rd_off), 1, h->st);
     if (e != cudaSuccess) return cuda_error(e, "readout reduce");
     for (size_t i = 0; i < rev.size(); ++i) {
         const Shape& sh = sha[rev[i].shape];
-        SweepLaunch L{sh.K, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
-                      reinterpret_cast<const int64_t*>(dblob + rev_pre[i])};
-        e = launch_sweep(L, grid_for(h, sh.K, 1), h->st);
+        SweepLaunch L{sh.kind, 0, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
+                      reinterpret_cast<const int64_t*>(dblob + rev_pre[i]), derr};
+        e = launch_sweep(L, grid_for(h, sh.kind, 1), h->st);
         if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
         if (red_cnt[i]) {
             e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + red_off[i]), red_cnt[i], h->st);
             if (e != cudaSuccess) return cuda_error(e, "adjoint reduce");
         }
     }
-    (void)cf;
-    (void)value; (void)dgamma; (void)dbeta;
     return QS_OK;
 }
 
@@ -495,7 +499,7 @@ int qs_evolve(qs_handle h, int p, const double* gamma, const double* beta, int f
     if (int rc = check_angles(p, gamma, beta)) return rc;
     const bool plain = h->path == QS_PATH_PLAIN;
     if (int rc = prepare_layers(h, p, gamma, beta, from_plus != 0, false, plain)) return rc;
-    int rc = plain ? run_plain(h, p, from_plus != 0) : run_tiled(h, p, from_plus != 0, 0, 0, nullptr, nullptr, nullptr);
+    int rc = plain ? run_plain(h, p, from_plus != 0) : run_tiled(h, p, from_plus != 0, 0, 0);
     if (rc) return rc;
     if (!plain) {
         cudaError_t e = launch_set_frame(reinterpret_cast<int*>(h->frame.ptr),
@@ -518,6 +522,7 @@ int qs_readout(qs_handle h, double* E, double* P, double* norm) {
     cudaError_t e = cudaMemcpyAsync(r, h->out.ptr, sizeof r, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_error(e, "readout");
+    if (int rc = check_device_error(h)) return rc;
     const double sc = std::ldexp(1.0, -h->inst.shift);
     if (E) *E = r[0] * sc;
     if (P) *P = r[1];
@@ -578,11 +583,12 @@ int qs_grad(qs_handle h, int p, const double* gamma, const double* beta, int obj
         h->own_lam = true;
     }
     if (int rc = prepare_layers(h, p, gamma, beta, true, true, false)) return rc;
-    if (int rc = run_tiled(h, p, true, 1, objective, value, dgamma, dbeta)) return rc;
+    if (int rc = run_tiled(h, p, true, 1, objective)) return rc;
     std::vector<double> r(3 + 2 * (size_t)p);
     cudaError_t e = cudaMemcpyAsync(r.data(), h->out.ptr, r.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_error(e, "qs_grad");
+    if (int rc = check_device_error(h)) return rc;
     const double sc = std::ldexp(1.0, -h->inst.shift);
     const double lam_sc = objective == QS_OBJ_ENERGY ? sc : 1.0;
     if (value) *value = objective == QS_OBJ_ENERGY ? r[0] * sc : r[1];
@@ -656,7 +662,7 @@ int qs_canonicalize(qs_handle h) {
 int qs_plan_info(qs_handle h, int p, int* tile_shapes, int* sweeps) {
     if (!h) return set_error(QS_EINVAL, "NULL handle");
     if (p < 0) return set_error(QS_EINVAL, "p < 0");
-    const auto sh = make_shapes(h->nphys, kernel_cfg(h->dtype, false));
+    const auto sh = make_shapes(h->nphys, kernel_cfg(h->dtype, false), page_bit_for(h->dtype));
     if (tile_shapes) *tile_shapes = (int)sh.size();
     if (sweeps) *sweeps = (int)plan_forward((int)sh.size(), p, true).size();
     return QS_OK;
@@ -667,9 +673,26 @@ int qs_plan_sweeps(int n, int dtype, int p, int* tile_shapes, int* sweeps) {
     const int nmax = dtype == QS_C64 ? QS_MAX_QUBITS_C64 : QS_MAX_QUBITS_C128;
     if (n < 1 || n > nmax || p < 0) return set_error(QS_EINVAL, "qs_plan_sweeps: bad n or p");
     const int nphys = n < kMinPhysQubits ? kMinPhysQubits : n;
-    const auto sh = make_shapes(nphys, kernel_cfg(dtype, false));
+    const auto sh = make_shapes(nphys, kernel_cfg(dtype, false), page_bit_for(dtype));
     if (tile_shapes) *tile_shapes = (int)sh.size();
     if (sweeps) *sweeps = (int)plan_forward((int)sh.size(), p, true).size();
+    return QS_OK;
+}
+
+int qs_plan_shape(int n, int dtype, int k, int* kind, int* K, int* c, int* g0, int* n1, int* g1) {
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_plan_shape: bad dtype");
+    const int nmax = dtype == QS_C64 ? QS_MAX_QUBITS_C64 : QS_MAX_QUBITS_C128;
+    if (n < 1 || n > nmax) return set_error(QS_EINVAL, "qs_plan_shape: bad n");
+    const int nphys = n < kMinPhysQubits ? kMinPhysQubits : n;
+    const auto sh = make_shapes(nphys, kernel_cfg(dtype, false), page_bit_for(dtype));
+    if (k < 0 || k >= (int)sh.size()) return set_error(QS_EINVAL, "qs_plan_shape: no shape %d", k);
+    const Shape& s = sh[k];
+    if (kind) *kind = s.kind;
+    if (K) *K = s.K;
+    if (c) *c = s.c;
+    if (g0) *g0 = s.g0;
+    if (n1) *n1 = s.n1;
+    if (g1) *g1 = s.g1;
     return QS_OK;
 }
 

@@ -23,7 +23,7 @@ using namespace qs;
 namespace {
 
 struct Launch {
-    int K, adjoint;
+    int kind, adjoint, variant, group;
     int ntasks;
     int64_t total_tiles;
     size_t task_off, pre_off;  // byte offsets in the uploaded blob
@@ -38,7 +38,7 @@ struct Wave {
 struct Blob {
     std::vector<unsigned char> b;
     size_t add(const void* p, size_t n) {
-        size_t off = (b.size() + 15) & ~size_t(15);
+        size_t off = (b.size() + 63) & ~size_t(63);  // keeps tensor maps 64-byte aligned
         b.resize(off + n);
         if (n) std::memcpy(b.data() + off, p, n);
         return off;
@@ -59,7 +59,7 @@ struct qs_batch {
     std::vector<int64_t> aoff;
     int64_t total = 0;
     std::vector<double> host_angles;  // [gamma_all, beta_all]
-    DevBuf angles, grads, adam_m, adam_v, step;
+    DevBuf angles, grads, adam_m, adam_v, step, err;
     DevBuf layers_f, layers_r, tab_f, tab_r, partials, out, frames;
     std::vector<size_t> lay_off, tab_off;  // per instance: LayerDev index / table element offsets
     Uploader up;
@@ -73,11 +73,21 @@ struct qs_batch {
     int objective = 0;
 };
 
-static int bgrid(qs_batch_handle b, int K, int adjoint) {
-    const KernelCfg cfg = kernel_cfg(b->dtype, adjoint != 0);
-    int& g = b->grid[adjoint][K == cfg.K_A ? 0 : 1];
-    if (!g) g = sweep_grid(K, adjoint, b->dtype);
+static int bgrid(qs_batch_handle b, int kind, int adjoint) {
+    int& g = b->grid[adjoint][kind];
+    if (!g) g = sweep_grid(b->dtype, adjoint, kind);
     return g;
+}
+
+// After a synchronisation: report (and clear) a timed-out device wait.
+static int batch_check_err(qs_batch_handle b) {
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, b->err.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "error word");
+    if (!v) return QS_OK;
+    cudaMemset(b->err.ptr, 0, sizeof(int));
+    b->have_results = false;
+    return set_error(QS_ETIMEOUT, "a sweep kernel gave up waiting for a tile copy; results are invalid");
 }
 
 static void drop_graph(qs_batch_handle b) {
@@ -105,9 +115,12 @@ int qs_batch_create(qs_batch_handle* out, int count, const int* n, int dtype, vo
         const int np = n[i] < kMinPhysQubits ? kMinPhysQubits : n[i];
         b->nphys.push_back(np);
         b->st_off.push_back(total);
-        total += (size_t)1 << np;  // 2^12 elements keep every state 256-byte aligned
+        total += (size_t)1 << np;  // >= 2^13 elements keep every state 256-byte aligned
     }
     if (int rc = b->states.reserve(total * 8)) return rc;
+    if (int rc = b->err.reserve(sizeof(int))) return rc;
+    e = cudaMemset(b->err.ptr, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "qs_batch_create");
     b->inst.resize(count);
     *out = b.release();
     return QS_OK;
@@ -166,7 +179,6 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
         maxf = std::max(maxf, fwd[i].size());
         maxr = std::max(maxr, rev[i].size());
     }
-    const int K_A = kernel_cfg(b->dtype, false).K_A;
     double* dout = reinterpret_cast<double*>(b->out.ptr);
     double* dgr = reinterpret_cast<double*>(b->grads.ptr);
     float2* states = reinterpret_cast<float2*>(b->states.ptr);
@@ -205,14 +217,14 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
             for (int kind = 0; kind < 2; ++kind) {
                 std::vector<SweepTask> tasks;
                 std::vector<int64_t> pre{0};
-                int K = 0;
+                int variant = 2;  // leanest kernel that serves every task of the launch
                 for (int i = 0; i < C; ++i) {
                     if (w >= L[i].size()) continue;
                     const PlanSweep& s = L[i][w];
                     const Instance& I = b->inst[i];
                     const Shape& sh = I.shapes[adj][s.shape];
-                    if ((sh.K == K_A) != (kind == 0)) continue;
-                    K = sh.K;
+                    if (sh.kind != kind) continue;
+                    variant = std::min(variant, sweep_variant(s.flags, s.nr, s.r));
                     SweepTask t;
                     std::memset(&t, 0, sizeof t);
                     t.psi = states + b->st_off[i];
@@ -236,6 +248,9 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
                     t.amp0 = std::pow(2.0, -0.5 * b->nphys[i]);
                     t.np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
                     for (int r = 0; r < s.nr; ++r) t.rounds[r] = s.r[r];
+                    t.kind = sh.kind;
+                    t.n1 = sh.n1;
+                    t.g1 = sh.g1;
                     // partial slots of this task: [pbase, pbase + ntiles) in units of np doubles
                     const double* tp = dpart + pbase;
                     if (t.np) {
@@ -264,8 +279,10 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
                 }
                 if (tasks.empty()) continue;
                 Launch l;
-                l.K = K;
+                l.kind = kind;
                 l.adjoint = adj;
+                l.variant = variant;
+                l.group = 1;
                 l.ntasks = (int)tasks.size();
                 l.total_tiles = pre.back();
                 l.task_off = blob.add(tasks.data(), tasks.size() * sizeof(SweepTask));
@@ -307,10 +324,11 @@ static int run_waves(qs_batch_handle b, const std::vector<Wave>& waves) {
     const unsigned char* d = reinterpret_cast<const unsigned char*>(b->up.dev.ptr);
     for (const Wave& w : waves) {
         for (const Launch& l : w.launches) {
-            SweepLaunch L{l.K, l.adjoint, b->dtype, l.ntasks, l.total_tiles,
+            SweepLaunch L{l.kind, l.variant, l.adjoint, b->dtype, l.ntasks, l.total_tiles,
                           reinterpret_cast<const SweepTask*>(d + l.task_off),
-                          reinterpret_cast<const int64_t*>(d + l.pre_off)};
-            cudaError_t e = launch_sweep(L, bgrid(b, l.K, l.adjoint), b->st);
+                          reinterpret_cast<const int64_t*>(d + l.pre_off), reinterpret_cast<int*>(b->err.ptr),
+                          l.group};
+            cudaError_t e = launch_sweep(L, bgrid(b, l.kind, l.adjoint), b->st);
             if (e != cudaSuccess) return cuda_error(e, "batched sweep");
         }
         if (w.nred) {
@@ -399,6 +417,7 @@ int qs_batch_results(qs_batch_handle b, double* E, double* P) {
     cudaError_t e = cudaMemcpyAsync(r.data(), b->out.ptr, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return cuda_error(e, "qs_batch_results");
+    if (int rc = batch_check_err(b)) return rc;
     for (int i = 0; i < b->count; ++i) {
         if (E) E[i] = r[3 * i];
         if (P) P[i] = r[3 * i + 1];
@@ -421,6 +440,7 @@ int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamm
         e = cudaMemcpyAsync(r.data(), b->out.ptr, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return cuda_error(e, "qs_batch_grad");
+    if (int rc = batch_check_err(b)) return rc;
     for (int i = 0; i < b->count; ++i) {
         if (value) value[i] = objective == QS_OBJ_ENERGY ? r[3 * i] : r[3 * i + 1];
         for (int k = 0; k < b->p[i]; ++k) {
@@ -510,6 +530,7 @@ int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2,
     e = cudaMemcpyAsync(a.data(), b->angles.ptr, a.size() * sizeof(double), cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return cuda_error(e, "qs_batch_adam");
+    if (int rc = batch_check_err(b)) return rc;
     for (int i = 0; i < b->count; ++i)
         for (int k = 0; k < b->p[i]; ++k) {
             gamma_io[b->aoff[i] + k] = a[b->aoff[i] + k];

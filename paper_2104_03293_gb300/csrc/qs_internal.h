@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace qs {
@@ -21,7 +22,7 @@ namespace qs {
 // bits [g0, g0 + K - c) whose x-rotations the sweep applies.  The first shape
 // (shape A) has c = 0 and targets [0, K_A).
 // ---------------------------------------------------------------------------
-constexpr int kMinPhysQubits = 12;   // states with n < 12 are padded with idle qubits
+constexpr int kMinPhysQubits = 13;   // states with n < 13 are padded with idle qubits
 constexpr int kMaxRounds = 8;        // rounds (layers) fused into one sweep
 constexpr int kMaxShapes = 4;        // tile shapes per plan
 constexpr int kMaxLayouts = 3;       // register layouts per tile shape
@@ -62,6 +63,8 @@ struct LayerDev {
 };
 
 struct SweepTask {
+    int kind;                    // 0 contiguous, 1 strided
+    int n1, g1;                  // strided: second target run (see Shape)
     void* psi;
     void* lam;
     const LayerDev* layers;
@@ -82,13 +85,16 @@ struct SweepTask {
 
 // A sweep over a list of tasks (one tile shape per launch).
 struct SweepLaunch {
-    int K;                 // tile bits (selects the kernel)
+    int kind;              // tile kind (selects the kernel with dtype / adjoint / variant)
+    int variant;           // 0 full, 1 phase, 2 rotations only (sweep_variant)
     int adjoint;
     int dtype;
     int ntasks;
     int64_t total_tiles;
     const SweepTask* tasks;        // device
     const int64_t* tile_prefix;    // device, ntasks + 1
+    int* err;                      // device error word (set on a timed-out wait)
+    int group = 1;                 // consecutive tiles per CTA turn (a power of 2)
 };
 
 // Cost program: the Ising cost of Eq. (HC) specialised to one register layout.
@@ -108,7 +114,9 @@ cudaError_t note_launch(cudaError_t e, int kernels = 1);
 int64_t launch_total();
 
 cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st);
-int sweep_grid(int K, int adjoint, int dtype);   // persistent grid size
+int sweep_grid(int dtype, int adjoint, int kind);   // persistent grid size
+// Leanest kernel variant that can run a sweep with these flags and rounds.
+int sweep_variant(int flags, int nrounds, const SweepRound* rounds);
 
 // Layer preparation: angles -> LayerDev + phase tables (forward or reverse).
 cudaError_t launch_prep(int dtype, int p, const double* gamma, const double* beta, int nphys,

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "qs_layout.h"
 #include "qs_plan.h"
 
 namespace qs {
@@ -134,37 +135,71 @@ int validate_ising(int n, const double* hfield, int n_edges, const int32_t* edge
     return 0;
 }
 
-std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg) {
+// Shape A: contiguous tiles of 2^K_A amplitudes rotating qubits [0, K_A - 1)
+// (two 2^(K_A - 1) blocks per tile).  Then strided shapes of K_B tile bits,
+// each rotating the next K_B - c_min qubits (fewer for the last one, which
+// then carries more low bits so that every tile keeps K_B bits).
+//
+// The strided shapes split the remaining qubits [K_A - 1, n).  A tile's rows
+// sit 2^(lowest target bit) apart, so a target run above the page bit
+// (2 MB pages: 2^18 complex64 amplitudes) makes every row of the tile land in
+// a different page: a tile with t such targets touches 2^t pages at once.  The
+// qubits between K_A - 1 and the page bit are therefore dealt out evenly, one
+// low run per strided shape, and each shape fills up with a high run.
+std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit) {
     std::vector<Shape> v;
     Shape a;
-    a.K = cfg.K_A; a.c = 0; a.g0 = 0; a.nt = cfg.K_A;
+    a.K = cfg.K_A; a.c = 0; a.g0 = 0; a.nt = cfg.K_A - 1; a.kind = 0; a.n1 = 0; a.g1 = 0;
     a.ntiles = (int64_t)1 << (nphys - cfg.K_A);
     v.push_back(a);
-    int g = cfg.K_A;
-    while (g < nphys) {
+    const int lo = cfg.K_A - 1;
+    const int per = cfg.K_B - cfg.c_min;                   // targets per strided shape
+    const int rest = nphys - lo;
+    if (rest <= 0) return v;
+    const int S = (rest + per - 1) / per;                  // strided shapes
+    const int below = std::max(0, std::min(page_bit, nphys) - lo);  // qubits below the page bit
+    const int high = rest - below;
+    // water-filling: deal the high qubits one at a time to the shape holding
+    // the fewest, so that the largest page footprint is as small as possible
+    std::vector<int> nt(S), nh(S, 0);
+    for (int k = 0; k < S; ++k) nt[k] = std::min(per, rest - k * per);
+    for (int i = 0; i < high; ++i) {
+        int best = -1;
+        for (int k = 0; k < S; ++k)
+            if (nh[k] < nt[k] && (best < 0 || nh[k] < nh[best])) best = k;
+        nh[best]++;
+    }
+    int lo_next = lo, hi_next = lo + below;
+    for (int k = 0; k < S; ++k) {
         Shape s;
         s.K = cfg.K_B;
-        s.nt = std::min(cfg.K_B - cfg.c_min, nphys - g);
-        s.c = cfg.K_B - s.nt;
-        s.g0 = g;
+        s.kind = 1;
+        s.nt = nt[k];
+        s.c = cfg.K_B - nt[k];
+        s.n1 = nt[k] - nh[k];
+        s.g0 = lo_next;
+        lo_next += s.n1;
+        s.g1 = nh[k] ? hi_next : s.g0 + s.n1;
+        hi_next += nh[k];
+        if (s.n1 == 0) s.g0 = s.g1;  // empty first run
         s.ntiles = (int64_t)1 << (nphys - cfg.K_B);
         v.push_back(s);
-        g += s.nt;
     }
+    // shapes whose low run ends where their high run starts are one run
+    for (auto& s : v)
+        if (s.kind == 1 && s.g0 + s.n1 == s.g1) { s.n1 = 0; s.g1 = s.g0; }
     return v;
 }
 
 void shape_regq(const Shape& s, int R, int g, int* regq) {
-    int lo = s.K - (g + 1) * R;
-    if (lo < 0) lo = 0;
+    const LayoutTab L = make_layout(s.K, R, s.kind);
     for (int b = 0; b < 6; ++b) {
-        if (b >= R) { regq[b] = -1; continue; }
-        const int tb = lo + b;
-        regq[b] = tb < s.c ? tb : s.g0 + (tb - s.c);
+        if (b >= R || g >= L.G) { regq[b] = -1; continue; }
+        regq[b] = shape_bit(s, L.regs[g][b]);
     }
 }
 
-int num_layouts(int K, int R) { return (K + R - 1) / R; }
+int num_layouts(const Shape& s, int R) { return make_layout(s.K, R, s.kind).G; }
 
 // Zig-zag schedule: layer k visits the shapes in order 0..S-1 (k even) or
 // S-1..0 (k odd).  The x-rotations of one layer commute, so the order inside a
@@ -225,13 +260,16 @@ std::vector<PlanSweep> plan_reverse(const std::vector<PlanSweep>& fwd, const std
 
 int count_sweeps(int nphys, int dtype, int p) {
     const KernelCfg cfg = kernel_cfg(dtype, false);
-    const auto sh = make_shapes(nphys, cfg);
+    const auto sh = make_shapes(nphys, cfg, page_bit_for(dtype));
     return (int)plan_forward((int)sh.size(), p, true).size();
 }
 
+// Tile bits and register bits per configuration.  complex64: 2^13-amplitude
+// tiles (64 KB); complex128: 2^12 (64 KB).  The adjoint holds psi and lambda,
+// so it keeps half as many amplitudes per thread on the same tiles.
 KernelCfg kernel_cfg(int dtype, bool adjoint) {
-    if (dtype == 0) return adjoint ? KernelCfg{12, 13, 5, 2} : KernelCfg{12, 13, 6, 2};
-    return adjoint ? KernelCfg{11, 12, 4, 2} : KernelCfg{11, 12, 5, 2};
+    if (dtype == 0) return adjoint ? KernelCfg{13, 13, 5, 2} : KernelCfg{13, 13, 6, 2};
+    return adjoint ? KernelCfg{12, 12, 4, 2} : KernelCfg{12, 12, 5, 2};
 }
 
 }  // namespace qs

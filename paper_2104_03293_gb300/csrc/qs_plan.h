@@ -20,10 +20,20 @@ struct IsingInt {
 int validate_ising(int n, const double* hfield, int n_edges, const int32_t* edges, const double* J, IsingInt& out,
                    std::string& err);
 
+// A tile shape (see qs_layout.h): kind 0 = 2^K contiguous amplitudes with
+// targets [0, K - 1); kind 1 = c carried low bits + nt = K - c targets in two
+// runs, [g0, g0 + n1) and [g1, g1 + nt - n1) (n1 may be 0).
 struct Shape {
-    int K, c, g0, nt;
+    int K, c, g0, nt, kind, n1, g1;
     int64_t ntiles;
 };
+
+// Global bit of tile bit tb of a shape.
+inline int shape_bit(const Shape& s, int tb) {
+    if (s.kind == 0 || tb < s.c) return tb;
+    if (tb < s.c + s.n1) return s.g0 + (tb - s.c);
+    return s.g1 + (tb - s.c - s.n1);
+}
 
 struct PlanSweep {
     int shape = 0;
@@ -32,9 +42,11 @@ struct PlanSweep {
     SweepRound r[kMaxRounds];
 };
 
-std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg);
+// Index bit at which a new 2 MB page starts (complex64: 8-byte amplitudes).
+inline int page_bit_for(int dtype) { return dtype == 0 ? 18 : 17; }
+std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit);
 void shape_regq(const Shape& s, int R, int g, int* regq);
-int num_layouts(int K, int R);
+int num_layouts(const Shape& s, int R);
 std::vector<PlanSweep> plan_forward(int S, int p, bool gen);
 std::vector<PlanSweep> plan_reverse(const std::vector<PlanSweep>& fwd, const std::vector<Shape>& shapes, int p);
 int count_sweeps(int nphys, int dtype, int p);

@@ -1,0 +1,663 @@
+#pragma once
+// Tiled HBM sweep kernel: one read + one write of the state (or of psi and
+// lambda) per launch, with the x-rotations of the tile's target bits
+// (Eq. twocomponentupdates applied to e^{-i beta X}, Sec. III.A.1), the
+// diagonal phase e^{-i gamma H_C} (Eq. HC, computed from the bit pattern, no
+// 2^n diagonal), the readout (<H_C>, ground probability, norm) and the adjoint
+// accumulations fused in.
+//
+// Persistent CTAs (two per SM for the forward sweep) walk over tiles of 2^K
+// amplitudes:
+//   * TMA brings a tile into the CTA's shared-memory tile buffer
+//     (cp.async.bulk.tensor boxes for strided tiles, cp.async.bulk for
+//     contiguous ones; mbarrier completion, bounded waits).  The load of the
+//     next tile is issued as soon as the current one has been read for the
+//     last time, so it overlaps the tile's remaining work and the other CTA.
+//   * each thread holds 2^R amplitudes per array in registers.  A layout
+//     (qs_layout.h) assigns R tile bits to the register slot index; the
+//     rotations of those bits are register butterflies.  Changing layout is a
+//     transpose through a swizzled shared-memory tile.
+//   * a round rotates every target once: the layouts in turn, then the next
+//     round walks them back, so two rounds share the layout at their boundary
+//     (the zig-zag inside a tile, matching the zig-zag of the sweep schedule).
+//   * the butterfly is the tangent form a' = a + w (-i b), |w| <= 1; the
+//     scalar per rotation is folded into the layer's phase table.
+//   * results leave from registers in layout 0 with coalesced stores.
+#include <type_traits>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "qs_internal.h"
+#include "qs_layout.h"
+
+namespace qs {
+
+template <class Real> struct C2T;
+template <> struct C2T<float> { using T = float2; };
+template <> struct C2T<double> { using T = double2; };
+
+template <class Real> __device__ __forceinline__ Real fma_(Real a, Real b, Real c) { return fma(a, b, c); }
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [Begin, End).
+template <int I, int End, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < End) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, End>(f);
+    }
+}
+
+// Shared-memory swizzle: phys(e) = e ^ ((e >> R) & 31).  It is linear
+// (phys(a ^ b) = phys(a) ^ phys(b)), so a thread's base and its compile-time
+// slot offsets combine with one XOR, and it makes every layout's accesses
+// conflict-free for the configurations in kernel_cfg (checked on the host by
+// the test-suite, tests/test_index_math.py).
+template <int R> struct Swz {
+    static constexpr int S = R;
+    __host__ __device__ static constexpr uint32_t phys(uint32_t e) { return e ^ ((e >> S) & 31u); }
+};
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier, giving up after ~2 s of device time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && globaltimer() - t0 > 2000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Contiguous copy global -> shared, completion on the barrier.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Index maps
+// ---------------------------------------------------------------------------
+// Strided tile map (kind 1): tile bits [0, c) are global bits [0, c); tile
+// bits [c, c + n1) are global [g0, g0 + n1); tile bits [c + n1, K) are global
+// [g1, g1 + K - c - n1).  The non-tile global bits, in ascending order, take
+// the tile index.
+struct TMap {
+    int c, g0, n1, g1, K;
+    __device__ __forceinline__ uint64_t gofs(uint32_t e) const {
+        const uint32_t cm = (1u << c) - 1u, m1 = (1u << n1) - 1u;
+        return (uint64_t)(e & cm) | ((uint64_t)((e >> c) & m1) << g0) | ((uint64_t)(e >> (c + n1)) << g1);
+    }
+    __device__ __forceinline__ uint64_t base(int64_t t) const {
+        const int la = g0 - c, lb = g1 - (g0 + n1);  // non-tile runs [c, g0), [g0 + n1, g1)
+        const uint64_t u = (uint64_t)t;
+        const uint64_t ma = la > 0 ? (1ull << la) - 1ull : 0ull, mb = lb > 0 ? (1ull << lb) - 1ull : 0ull;
+        return ((u & ma) << c) | (((u >> la) & mb) << (g0 + n1)) | ((u >> (la + lb)) << (g1 + K - c - n1));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Cost program evaluation (see build_cost_prog).
+// ---------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ int eval_cost(const int32_t* __restrict__ cp, uint64_t z, int (&fb)[R], const int32_t*& q) {
+    const int nf = __ldg(cp + 1), ne = __ldg(cp + 2), const0 = __ldg(cp + 3), qoff = __ldg(cp + 4);
+    const int32_t* t = cp + 12;
+    int acc = 0;
+#pragma unroll 4
+    for (int k = 0; k < nf; ++k) acc += __ldg(t + 2 * k + 1) * (int)((z >> __ldg(t + 2 * k)) & 1ull);
+    t += 2 * nf;
+#pragma unroll 4
+    for (int k = 0; k < ne; ++k) {
+        const int ij = __ldg(t + 2 * k), J = __ldg(t + 2 * k + 1);
+        acc += J * (int)(((z >> (ij & 255)) ^ (z >> (ij >> 8))) & 1ull);
+    }
+    t += 2 * ne;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+        const int fb0 = __ldg(t), cnt = __ldg(t + 1);
+        t += 2;
+        int a2 = 0;
+        for (int k = 0; k < cnt; ++k) a2 += __ldg(t + 2 * k + 1) * (int)((z >> __ldg(t + 2 * k)) & 1ull);
+        t += 2 * cnt;
+        fb[b] = fb0 - 2 * a2;
+    }
+    q = cp + qoff;
+    return const0 - 2 * acc;
+}
+
+// idx(m) = C(slot m) - cost_lo from two partial-sum tables over the low /
+// high halves of the register bits plus the intra-register coupling table Q.
+template <int R>
+struct SlotCost {
+    static constexpr int R1 = R / 2, R2 = R - R1;
+    int plo[1 << R1], phi[1 << R2];
+    const int32_t* q;
+    __device__ __forceinline__ void init(const int32_t* __restrict__ cp, uint64_t zt, int flip, int cost_lo) {
+        int fb[R];
+        const int cout = eval_cost<R>(cp, zt, fb, q);
+        if (flip) {
+#pragma unroll
+            for (int b = 0; b < R; ++b) fb[b] = -fb[b];
+        }
+        int base = cout - cost_lo;
+#pragma unroll
+        for (int b = 0; b < R1; ++b) base += fb[b];
+        plo[0] = base;
+#pragma unroll
+        for (int b = 0; b < R1; ++b)
+#pragma unroll
+            for (int k = 0; k < (1 << b); ++k) plo[k | (1 << b)] = plo[k] - 2 * fb[b];
+        int hb = 0;
+#pragma unroll
+        for (int b = 0; b < R2; ++b) hb += fb[R1 + b];
+        phi[0] = hb;
+#pragma unroll
+        for (int b = 0; b < R2; ++b)
+#pragma unroll
+            for (int k = 0; k < (1 << b); ++k) phi[k | (1 << b)] = phi[k] - 2 * fb[R1 + b];
+    }
+    __device__ __forceinline__ int idx(int m) const { return plo[m & ((1 << R1) - 1)] + phi[m >> R1] + __ldg(q + m); }
+    // table index, kept inside [0, top] so that no cost can address memory
+    // outside the phase table
+    __device__ __forceinline__ int tidx(int m, int top) const { return min(max(idx(m), 0), top); }
+};
+
+// Warp-level sum, lane 0 stores into red[warp * nslots + slot].
+__device__ __forceinline__ void warp_sum_to(double v, double* red, int slot, int nslots) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[(threadIdx.x >> 5) * nslots + slot] = v;
+}
+
+// ---------------------------------------------------------------------------
+// The sweep
+// ---------------------------------------------------------------------------
+template <class Real, int K, int R, int NA, int KIND>
+struct Sweep {
+    using C2 = typename C2T<Real>::T;
+    // layout tables as compile-time scalars (qs_layout.h)
+    static constexpr int G = make_layout(K, R, KIND).G;
+    template <int g, int b> __host__ __device__ static constexpr int reg_bit() { return make_layout(K, R, KIND).regs[g][b]; }
+    template <int g, int j> __host__ __device__ static constexpr int thr_bit() { return make_layout(K, R, KIND).tbits[g][j]; }
+    template <int g> __host__ __device__ static constexpr int rot_lo() { return make_layout(K, R, KIND).rot_lo[g]; }
+    template <int g> __host__ __device__ static constexpr int rot_hi() { return make_layout(K, R, KIND).rot_hi[g]; }
+    static constexpr int NT = 1 << (K - R);
+    static constexpr int NS = 1 << R;
+    static constexpr int NW = NT / 32;
+    static constexpr int NSLOT = 2 * kMaxRounds;
+    static constexpr size_t TILE_BYTES = (size_t)sizeof(C2) << K;
+    static constexpr size_t BUF_BYTES = (size_t)NA * TILE_BYTES;  // one region per array
+    static constexpr size_t SMEM_BYTES = BUF_BYTES + 64 + (size_t)NW * NSLOT * 8;
+    static_assert(K - R >= 5, "a tile needs at least one full warp");
+    static_assert(G <= kMaxLay, "too many layouts");
+
+    template <int g>
+    __device__ static __forceinline__ uint32_t e_thread(uint32_t tid) {
+        uint32_t e = 0;
+        static_for<0, K - R>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            e |= ((tid >> j) & 1u) << thr_bit<g, j>();
+        });
+        return e;
+    }
+    template <int g>
+    __device__ static __forceinline__ uint32_t e_slot(int m) {
+        uint32_t e = 0;
+        static_for<0, R>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            e |= (uint32_t)((m >> b) & 1) << reg_bit<g, b>();
+        });
+        return e;
+    }
+
+    // ---- shared-memory transposes ------------------------------------------
+    template <int g>
+    __device__ static __forceinline__ void sts(C2* tb, const C2 (&x)[NS], uint32_t tid) {
+        const uint32_t pt = Swz<R>::phys(e_thread<g>(tid));
+#pragma unroll
+        for (int m = 0; m < NS; ++m) tb[pt ^ Swz<R>::phys(e_slot<g>(m))] = x[m];
+    }
+    template <int g>
+    __device__ static __forceinline__ void lds(const C2* tb, C2 (&x)[NS], uint32_t tid) {
+        const uint32_t pt = Swz<R>::phys(e_thread<g>(tid));
+#pragma unroll
+        for (int m = 0; m < NS; ++m) x[m] = tb[pt ^ Swz<R>::phys(e_slot<g>(m))];
+    }
+    template <int g>
+    __device__ static __forceinline__ void lds_dense(const C2* src, C2 (&x)[NS], uint32_t tid) {
+        const uint32_t et = e_thread<g>(tid);
+#pragma unroll
+        for (int m = 0; m < NS; ++m) x[m] = src[et | e_slot<g>(m)];
+    }
+    __device__ static __forceinline__ void sts_any(int g, C2* tb, const C2 (&x)[NS], uint32_t tid) {
+        if (g == 0) sts<0>(tb, x, tid);
+        else if (G > 1 && g == 1) sts<(G > 1 ? 1 : 0)>(tb, x, tid);
+        else if (G > 2) sts<(G > 2 ? 2 : 0)>(tb, x, tid);
+    }
+    __device__ static __forceinline__ void lds_any(int g, const C2* tb, C2 (&x)[NS], uint32_t tid) {
+        if (g == 0) lds<0>(tb, x, tid);
+        else if (G > 1 && g == 1) lds<(G > 1 ? 1 : 0)>(tb, x, tid);
+        else if (G > 2) lds<(G > 2 ? 2 : 0)>(tb, x, tid);
+    }
+    // In place: each array has its own region of the tile buffer.  A thread
+    // rewrites exactly the slots it last read in layout `from`, so only the
+    // barrier between the writes and the reads of layout `to` is needed.
+    __device__ static __forceinline__ void transpose(int from, int to, C2* buf, C2 (&v)[NA][NS], uint32_t tid) {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) sts_any(from, buf + ((size_t)a << K), v[a], tid);
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < NA; ++a) lds_any(to, buf + ((size_t)a << K), v[a], tid);
+    }
+
+    // ---- rotations ---------------------------------------------------------
+    // Butterfly on register bit b:  a' = a + w (-i b),  b' = b + w (-i a).
+    // Adjoint (NA = 2): before it, gacc += fpow * Im(conj(lam_a) psi_b +
+    // conj(lam_b) psi_a), with fpow = |f|^{2r} for the r rotations of this
+    // layer already applied (the stored states carry f^{-r}).
+    template <int g>
+    __device__ static __forceinline__ void rotate(C2 (&v)[NA][NS], Real w, int c, Real fabs2, Real& fpow,
+                                                  Real& gacc) {
+        static_for<0, R>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int tb = reg_bit<g, b>();
+            constexpr int rk = rank_of(K, KIND, tb);
+            if constexpr (rk < rot_lo<g>() || rk >= rot_hi<g>()) return;  // not rotated in this layout
+            if (KIND == 1 && tb < c) return;                             // carried bit
+            Real part = 0;
+#pragma unroll
+            for (int m = 0; m < NS; ++m) {
+                if (m & (1 << b)) continue;
+                const int m2 = m | (1 << b);
+                if (NA == 2) {
+                    const C2 pa = v[0][m], pb = v[0][m2], la = v[NA - 1][m], lb = v[NA - 1][m2];
+                    Real t0 = la.x * pb.y - la.y * pb.x;
+                    t0 = fma_(lb.x, pa.y, t0);
+                    t0 = fma_(-lb.y, pa.x, t0);
+                    part += t0;
+                }
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const C2 x = v[a][m], y = v[a][m2];
+                    C2 nx, ny;
+                    nx.x = fma_(w, y.y, x.x);
+                    nx.y = fma_(-w, y.x, x.y);
+                    ny.x = fma_(w, x.y, y.x);
+                    ny.y = fma_(-w, x.x, y.y);
+                    v[a][m] = nx;
+                    v[a][m2] = ny;
+                }
+            }
+            if (NA == 2) {
+                gacc = fma_(part, fpow, gacc);
+                fpow *= fabs2;
+            }
+        });
+    }
+    __device__ static __forceinline__ void rotate_any(int g, C2 (&v)[NA][NS], Real w, int c, Real fabs2, Real& fpow,
+                                                      Real& gacc) {
+        if (g == 0) rotate<0>(v, w, c, fabs2, fpow, gacc);
+        else if (G > 1 && g == 1) rotate<(G > 1 ? 1 : 0)>(v, w, c, fabs2, fpow, gacc);
+        else if (G > 2) rotate<(G > 2 ? 2 : 0)>(v, w, c, fabs2, fpow, gacc);
+    }
+
+    // ---- phase -------------------------------------------------------------
+    template <int g>
+    __device__ static __forceinline__ void phase(C2 (&v)[NA][NS], const SweepTask& T, uint64_t zthread,
+                                                 const C2* __restrict__ tab, int frame, Real& gacc) {
+        const uint64_t fm = frame ? ((1ull << T.n) - 1ull) : 0ull;
+        SlotCost<R> sc;
+        sc.init(T.cprog[g], zthread ^ fm, frame, T.cost_lo);
+        const int top = T.tab_stride - 1;
+        Real part = 0;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+            const int ix = sc.tidx(m, top);
+            const C2 f = __ldg(tab + ix);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const C2 x = v[a][m];
+                C2 y;
+                y.x = fma_(x.x, f.x, -x.y * f.y);
+                y.y = fma_(x.x, f.y, x.y * f.x);
+                v[a][m] = y;
+            }
+            if (NA == 2) {
+                const Real im = v[NA - 1][m].x * v[0][m].y - v[NA - 1][m].y * v[0][m].x;
+                part = fma_((Real)(ix + T.cost_lo), im, part);
+            }
+        }
+        gacc += part;
+    }
+
+    // global offset of the thread part of layout g
+    template <int g>
+    __device__ static __forceinline__ uint64_t zthread(uint64_t base, uint32_t tid, const TMap& tm) {
+        const uint32_t e = e_thread<g>(tid);
+        return base + (KIND == 0 ? (uint64_t)e : tm.gofs(e));
+    }
+    __device__ static __forceinline__ void phase_any(int g, C2 (&v)[NA][NS], const SweepTask& T, const TMap& tm,
+                                                     uint64_t base, uint32_t tid, const C2* tab, int frame,
+                                                     Real& gacc) {
+        if (g == 0) phase<0>(v, T, zthread<0>(base, tid, tm), tab, frame, gacc);
+        else if (G > 1 && g == 1)
+            phase<(G > 1 ? 1 : 0)>(v, T, zthread<(G > 1 ? 1 : 0)>(base, tid, tm), tab, frame, gacc);
+        else if (G > 2)
+            phase<(G > 2 ? 2 : 0)>(v, T, zthread<(G > 2 ? 2 : 0)>(base, tid, tm), tab, frame, gacc);
+    }
+
+    // ---- layout-0 global offsets of the register slots ----------------------
+    // kind 0: compile-time; kind 1: layout 0's registers are the top R tile
+    // bits.  When they all lie in the last target run (every large shape)
+    // the offset is one shift; otherwise the general map.
+    template <class F>
+    __device__ static __forceinline__ void for_slots(const TMap& tm, F&& f) {
+        if (KIND == 0) {
+#pragma unroll
+            for (int m = 0; m < NS; ++m) f(m, (uint64_t)e_slot<0>(m));
+        } else {
+            constexpr int lo = K - R;  // regs of layout 0 are tile bits [K - R, K)
+            if (tm.c + tm.n1 <= lo) {
+                const int sh = tm.g1 + lo - tm.c - tm.n1;
+#pragma unroll
+                for (int m = 0; m < NS; ++m) f(m, (uint64_t)m << sh);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NS; ++m) f(m, tm.gofs((uint32_t)m << lo));
+            }
+        }
+    }
+};
+
+// Kernel variants: FULL has every feature; PHASE (middle sweeps with a layer
+// boundary) drops |+> generation, readout and lambda; LEAN (middle sweeps
+// without a phase) also drops the phase.  Leaner variants keep the
+// instruction footprint of the hot loop small.
+enum : int { V_FULL = 0, V_PHASE = 1, V_LEAN = 2 };
+
+template <class Real, int K, int R, int NA, int KIND, int V>
+__global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
+    sweep_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks, int64_t total,
+                 int* __restrict__ err, int qlog) {
+    using S = Sweep<Real, K, R, NA, KIND>;
+    using C2 = typename S::C2;
+    constexpr int NS = S::NS, NW = S::NW, NSLOT = S::NSLOT;
+    constexpr bool kGen = V == V_FULL, kPhase = V != V_LEAN, kRead = V == V_FULL;
+    static_assert(KIND == 0 || make_layout(K, R, KIND).regs[0][0] == K - R, "layout 0 holds the top R tile bits");
+    extern __shared__ __align__(128) unsigned char smraw[];
+    C2* buf = reinterpret_cast<C2*>(smraw);                                      // [NA][2^K]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smraw + S::BUF_BYTES);
+    double* red = reinterpret_cast<double*>(smraw + S::BUF_BYTES + 64);
+    const uint32_t tid = threadIdx.x;
+    C2 v[NA][NS];
+
+    auto find_task = [&](int64_t gt) -> int {
+        if (ntasks == 1) return 0;
+        int lo = 0, hi = ntasks - 1;  // last task whose prefix <= gt
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(prefix + mid) <= gt) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    };
+    // Thread 0: TMA loads of global tile gt into the tile buffer.
+    bool pending = false;
+    // Called by every thread.  Contiguous tiles: thread 0 issues one TMA bulk
+    // copy per array.  Strided tiles: every thread issues 16-byte cp.async
+    // copies (each request exactly one 32-byte sector of a row), completing on
+    // the same barrier.
+    auto issue = [&](int64_t gt) {
+        const int ti = find_task(gt);
+        const SweepTask& T = tasks[ti];
+        if (kGen && (T.flags & T_GEN)) return;  // generated, nothing to load
+        const int64_t tile = gt - __ldg(prefix + ti);
+        if (KIND == 1) {
+            constexpr int EPC = 16 / (int)sizeof(C2);                  // elements per 16-byte copy
+            constexpr int CHUNKS = (1 << K) / EPC;
+            const TMap tm{T.c, T.g0, T.n1, T.g1, K};
+            const uint64_t base = tm.base(tile);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const C2* src = reinterpret_cast<const C2*>(a == 0 ? T.psi : T.lam) + base;
+                C2* dst = buf + ((size_t)a << K);
+                for (int q = tid; q < CHUNKS; q += S::NT) {
+                    const uint32_t e = (uint32_t)q * EPC;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + e)),
+                                 "l"(src + tm.gofs(e))
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full)) : "memory");
+            pending = true;
+            return;
+        }
+        if (tid != 0) return;
+        mbar_expect_tx(full, (uint32_t)S::BUF_BYTES);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const C2* src = reinterpret_cast<const C2*>(a == 0 ? T.psi : T.lam) + ((uint64_t)tile << K);
+            tma_load_1d(buf + ((size_t)a << K), src, (uint32_t)S::TILE_BYTES, full);
+        }
+        pending = true;
+    };
+
+    if (tid == 0) {
+        mbar_init(full, KIND == 1 ? S::NT : 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // The CTA's k-th tile: groups of 2^qlog consecutive tiles (which share
+    // HBM lines when rows are short) run back to back on one CTA.
+    const int64_t qmask = (1ll << qlog) - 1;
+    auto tile_at = [&](int64_t k) -> int64_t {
+        return (((int64_t)blockIdx.x + (k >> qlog) * gridDim.x) << qlog) + (k & qmask);
+    };
+    if (tile_at(0) < total) issue(tile_at(0));
+
+    uint32_t parity = 0;
+    for (int64_t k = 0;; ++k) {
+        const int64_t gt = tile_at(k);
+        if (gt >= total) break;
+        const int ti = find_task(gt);
+        const SweepTask& T = tasks[ti];
+        const int64_t tile = gt - __ldg(prefix + ti);
+        const int c = T.c, flags = T.flags, nr = T.nrounds;
+        const TMap tm{T.c, T.g0, T.n1, T.g1, K};
+        const uint64_t base = KIND == 0 ? ((uint64_t)tile << K) : tm.base(tile);
+        // layouts that hold targets (kind 1 drops those entirely below c)
+        int ga = S::G;
+        if (KIND == 1) {
+            ga = 1;
+            if (S::G > 1 && K - 1 - S::template rot_lo<(1 < S::G ? 1 : 0)>() >= c) ga = 2;
+            if (S::G > 2 && K - 1 - S::template rot_lo<(2 < S::G ? 2 : 0)>() >= c) ga = 3;
+        }
+        const bool gen = kGen && (flags & T_GEN);
+        const int start = (gen && (nr & 1) && ga > 1) ? ga - 1 : 0;
+        // transposes of this tile: ga - 1 per round, + 1 back to layout 0
+        const int endl = ga == 1 ? 0 : ((start == 0) == ((nr & 1) == 0) ? 0 : ga - 1);
+        const int ntr = nr * (ga - 1) + (endl != 0 ? 1 : 0);
+        int done_tr = 0;
+        const int64_t nx = tile_at(k + 1);
+        // after the tile's last shared-memory read: reload the buffer
+        auto release = [&]() {
+            __syncthreads();
+            if (nx < total) {
+                if (tid == 0 && KIND == 0) fence_proxy_async();
+                issue(nx);
+            }
+        };
+        const uint64_t g_thread = S::template zthread<0>(base, tid, tm);
+        C2* arr[2] = {reinterpret_cast<C2*>(T.psi), reinterpret_cast<C2*>(T.lam)};
+
+        int cur = start;
+        if (gen) {
+            __syncthreads();  // the previous tile's reads of the buffer are done
+            const Real a0 = (Real)T.amp0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int m = 0; m < NS; ++m) v[a][m] = C2{a0, (Real)0};
+            if (ntr == 0 && nx < total) issue(nx);
+        } else {
+            const int ok = mbar_wait_bounded(full, parity) ? 1 : 0;
+            parity ^= 1u;
+            if (tid == 0) pending = false;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) atomicExch(err, 1);
+                break;
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a) S::template lds_dense<0>(buf + ((size_t)a << K), v[a], tid);
+            if (ntr == 0) release();
+            else __syncthreads();  // dense reads done before the swizzled writes
+        }
+        auto transpose = [&](int from, int to) {
+            S::transpose(from, to, buf, v, tid);
+            if (++done_tr == ntr) release();
+        };
+
+        const C2* tab = reinterpret_cast<const C2*>(T.tab);
+        for (int r = 0; r < nr; ++r) {
+            const SweepRound rd = T.rounds[r];
+            const LayerDev ly = T.layers[rd.layer];
+            Real gB = 0, gG = 0;
+            const C2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
+            if (kPhase && rd.phase_pre) S::phase_any(cur, v, T, tm, base, tid, ltab, ly.frame, gG);
+            const Real fabs2 = (Real)(ly.fabs * ly.fabs);
+            Real fpow = 1;
+            if (NA == 2) fpow = (Real)pow(ly.fabs, 2.0 * rd.r0);
+            const Real w = (Real)ly.w;
+            if (cur == 0) {
+                for (int g = 0; g < ga; ++g) {
+                    if (g != cur) { transpose(cur, g); cur = g; }
+                    S::rotate_any(g, v, w, c, fabs2, fpow, gB);
+                }
+            } else {
+                for (int g = ga - 1; g >= 0; --g) {
+                    if (g != cur) { transpose(cur, g); cur = g; }
+                    S::rotate_any(g, v, w, c, fabs2, fpow, gB);
+                }
+            }
+            if (kPhase && rd.phase_post) S::phase_any(cur, v, T, tm, base, tid, ltab, ly.frame, gG);
+            if (NA == 2) {
+                warp_sum_to((double)gB, red, 2 * r, NSLOT);
+                warp_sum_to((double)gG, red, 2 * r + 1, NSLOT);
+            }
+        }
+        if (cur != 0) { transpose(cur, 0); cur = 0; }
+
+        if (kRead && (flags & (T_READOUT | T_WRITE_LAM))) {
+            const int ef = T.layers[T.end_layer].frame;
+            const uint64_t fm = ef ? ((1ull << T.n) - 1ull) : 0ull;
+            SlotCost<R> sc;
+            sc.init(T.cprog[0], g_thread ^ fm, ef, T.cost_lo);
+            Real E = 0, P = 0, N = 0;
+            C2* lam = arr[1] + g_thread;
+            const bool wl = (flags & T_WRITE_LAM) != 0;
+            S::for_slots(tm, [&](int m, uint64_t off) {
+                const C2 x = v[0][m];
+                const int ix = sc.idx(m);
+                const Real w2 = x.x * x.x + x.y * x.y;
+                const Real cst = (Real)(ix + T.cost_lo);
+                E = fma_(w2, cst, E);
+                N += w2;
+                const bool gnd = (ix == T.gidx);
+                if (gnd) P += w2;
+                if (wl) {
+                    const Real o = (T.objective == 0) ? cst : (gnd ? (Real)1 : (Real)0);
+                    lam[off] = C2{o * x.x, o * x.y};
+                }
+            });
+            if (flags & T_READOUT) {
+                warp_sum_to((double)E, red, 0, NSLOT);
+                warp_sum_to((double)P, red, 1, NSLOT);
+                warp_sum_to((double)N, red, 2, NSLOT);
+            }
+        }
+        if (flags & T_STORE) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                C2* dst = arr[a] + g_thread;
+                S::for_slots(tm, [&](int m, uint64_t off) { dst[off] = v[a][m]; });
+            }
+        }
+        if ((kRead || NA == 2) && T.np > 0) {
+            const int np = T.np;
+            __syncthreads();
+            if (tid < (uint32_t)np) {
+                double s = 0.0;
+                for (int w = 0; w < NW; ++w) s += red[w * NSLOT + tid];
+                T.partials[(T.part_base + tile) * np + tid] = s;
+            }
+            __syncthreads();
+        }
+    }
+    // On a timeout, wait (bounded) for a copy still in flight before the CTA's
+    // shared memory goes away.
+    if (tid == 0 && pending) mbar_wait_bounded(full, parity);
+}
+
+template <class Real, int K, int R, int NA, int KIND, int V>
+cudaError_t launch_sweep_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
+    using S = Sweep<Real, K, R, NA, KIND>;
+    auto kern = sweep_kernel<Real, K, R, NA, KIND, V>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int qlog = 0;
+    while ((1 << (qlog + 1)) <= L.group) ++qlog;
+    kern<<<grid, S::NT, S::SMEM_BYTES, st>>>(L.tasks, L.tile_prefix, L.ntasks, L.total_tiles, L.err, qlog);
+    return note_launch(cudaGetLastError());
+}
+
+template <class Real, int K, int R, int NA, int KIND, int V>
+int grid_cfg() {
+    using S = Sweep<Real, K, R, NA, KIND>;
+    auto kern = sweep_kernel<Real, K, R, NA, KIND, V>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, S::SMEM_BYTES);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * sms;
+}
+
+}  // namespace qs

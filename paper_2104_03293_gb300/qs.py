@@ -65,6 +65,7 @@ _SIGS = {
     "qs_aqa_angles_2nd": [_I, _D, _PD, _PD, _PD],
     "qs_aqa_chain": [_I, _D, _PD, _PD, _PD, _PD, _PD],
     "qs_launch_count": [_PI64],
+    "qs_plan_shape": [_I, _I, _I, _PI, _PI, _PI, _PI, _PI, _PI],
     "qs_last_error": [],
     "qs_version": [],
     "qs_batch_create": [ctypes.POINTER(_P), _I, _PI, _I, _P],
@@ -243,6 +244,18 @@ def plan_sweeps(n: int, p: int, dtype: int = QS_C64):
     s, w = ctypes.c_int(), ctypes.c_int()
     _check(lib().qs_plan_sweeps(int(n), int(dtype), int(p), ctypes.byref(s), ctypes.byref(w)))
     return s.value, w.value
+
+
+def plan_shapes(n: int, dtype: int = QS_C64):
+    """Tile shapes of the tiled path: list of dicts (kind, K, c, g0, n1, g1)."""
+    out = []
+    for k in range(8):
+        vals = [ctypes.c_int() for _ in range(6)]
+        rc = lib().qs_plan_shape(int(n), int(dtype), k, *[ctypes.byref(v) for v in vals])
+        if rc != QS_OK:
+            break
+        out.append(dict(zip(("kind", "K", "c", "g0", "n1", "g1"), (v.value for v in vals))))
+    return out
 
 
 def aqa_angles(tau: float, s) -> tuple:

@@ -1,0 +1,108 @@
+"""Python restatement of the tile shapes, register layouts and index maps of
+the CUDA sweep (qs_layout.h, make_shapes, the kernel's address formulas), for
+host-side checks of the index arithmetic."""
+
+CFG = {("c64", False): (13, 13, 6, 2), ("c64", True): (13, 13, 5, 2),
+       ("c128", False): (12, 12, 5, 2), ("c128", True): (12, 12, 4, 2)}
+MIN_PHYS = 13
+
+
+def ranked_bit(K, kind, i):
+    if kind == 0:
+        return K - 2 - i if i < K - 1 else K - 1
+    return K - 1 - i
+
+
+def rank_of(K, kind, b):
+    if kind == 0:
+        return K - 1 if b == K - 1 else K - 2 - b
+    return K - 1 - b
+
+
+def make_layout(K, R, kind):
+    ntg = K - 1 if kind == 0 else K
+    G = -(-ntg // R)
+    out = []
+    for g in range(G):
+        if g * R + R <= ntg:
+            regs = sorted(ranked_bit(K, kind, i) for i in range(g * R, g * R + R))
+        else:
+            regs = list(range(R))
+        tbits = [b for b in range(K) if b not in regs]
+        out.append({"regs": regs, "tbits": tbits, "rot": (g * R, min((g + 1) * R, ntg))})
+    return out
+
+
+PAGE_BIT = {"c64": 18, "c128": 17}
+
+
+def make_shapes(nphys, KA, KB, cmin, page_bit=18):
+    shapes = [dict(K=KA, c=0, g0=0, nt=KA - 1, kind=0, n1=0, g1=0)]
+    lo = KA - 1
+    per = KB - cmin
+    rest = nphys - lo
+    if rest <= 0:
+        return shapes
+    S = -(-rest // per)
+    below = max(0, min(page_bit, nphys) - lo)
+    high = rest - below
+    nt = [min(per, rest - k * per) for k in range(S)]
+    nh = [0] * S
+    for _ in range(high):
+        best = min((k for k in range(S) if nh[k] < nt[k]), key=lambda k: (nh[k], k))
+        nh[best] += 1
+    lo_next, hi_next = lo, lo + below
+    for k in range(S):
+        n1 = nt[k] - nh[k]
+        g0 = lo_next
+        lo_next += n1
+        g1 = hi_next if nh[k] else g0 + n1
+        hi_next += nh[k]
+        if n1 == 0:
+            g0 = g1
+        if g0 + n1 == g1:
+            n1, g1 = 0, g0
+        shapes.append(dict(K=KB, c=KB - nt[k], g0=g0, nt=nt[k], kind=1, n1=n1, g1=g1))
+    return shapes
+
+
+def gofs(e, sh):
+    c, g0, n1, g1 = sh["c"], sh["g0"], sh["n1"], sh["g1"]
+    return (e & ((1 << c) - 1)) | (((e >> c) & ((1 << n1) - 1)) << g0) | ((e >> (c + n1)) << g1)
+
+
+def tile_base(t, sh):
+    K, c, g0, n1, g1 = sh["K"], sh["c"], sh["g0"], sh["n1"], sh["g1"]
+    if sh["kind"] == 0:
+        return t << K
+    la, lb = g0 - c, g1 - (g0 + n1)
+    ma = (1 << la) - 1 if la > 0 else 0
+    mb = (1 << lb) - 1 if lb > 0 else 0
+    return ((t & ma) << c) | (((t >> la) & mb) << (g0 + n1)) | ((t >> (la + lb)) << (g1 + K - c - n1))
+
+
+def tile_to_global(e, sh):
+    return e if sh["kind"] == 0 else gofs(e, sh)
+
+
+def slot_off0(m, sh, R, lay0):
+    """Global offset of register slot m in layout 0 (the kernel's for_slots)."""
+    K = sh["K"]
+    if sh["kind"] == 0:
+        return sum(((m >> b) & 1) << lay0["regs"][b] for b in range(R))
+    lo = K - R
+    if sh["c"] + sh["n1"] <= lo:
+        return m << (sh["g1"] + lo - sh["c"] - sh["n1"])
+    return gofs(m << lo, sh)
+
+
+def e_thread(t, lay):
+    return sum(((t >> j) & 1) << b for j, b in enumerate(lay["tbits"]))
+
+
+def e_slot(m, lay):
+    return sum(((m >> j) & 1) << b for j, b in enumerate(lay["regs"]))
+
+
+def phys(e, R):
+    return e ^ ((e >> R) & 31)

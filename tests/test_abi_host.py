@@ -71,50 +71,29 @@ def test_aqa_bad_arguments(lib):
 @pytest.mark.parametrize("n", [1, 11, 12, 13, 16, 23, 24, 25, 30, 33, 34])
 def test_zigzag_sweep_count(lib, n):
     """Shape A covers qubits 0..11, every further shape 11 more (2 carried low
-    bits).  With S shapes the zig-zag order merges one sweep per layer
-    boundary: p layers take (S - 1) p + 1 sweeps (S = 1: all layers share one
-    tile, up to 8 layers per sweep)."""
-    nphys = max(n, 12)
-    S = 1 + (max(0, nphys - 12) + 10) // 11
+    bits); states are stored with at least 13 qubits.  With S shapes the
+    zig-zag order merges one sweep per layer boundary: p layers take
+    (S - 1) p + 1 sweeps."""
+    nphys = max(n, 13)
+    S = 1 + (nphys - 12 + 10) // 11
     for p in (0, 1, 2, 3, 7, 20):
         s, w = qs.plan_sweeps(n, p)
         assert s == S
-        if p == 0:
-            assert w == 1
-        elif S == 1:
-            assert w == -(-p // 8)
-        else:
-            assert w == (S - 1) * p + 1
+        assert w == (1 if p == 0 else (S - 1) * p + 1)
 
 
-def _layouts(K, R):
-    G = -(-K // R)
-    out = []
-    for g in range(G):
-        lo = max(K - (g + 1) * R, 0)
-        regs = list(range(lo, lo + R))
-        thread = [b for b in range(K) if b not in regs]
-        out.append((regs, thread))
-    return out
-
-
-@pytest.mark.parametrize("K,R,elem", [(12, 6, 8), (13, 6, 8), (12, 5, 8), (13, 5, 8), (11, 5, 16), (12, 5, 16)])
-def test_swizzle_is_conflict_free(K, R, elem):
-    """phys(e) = e ^ ((e >> S) & 31), S = max(R, 5): for every layout, slot and
-    warp, the lanes of each shared-memory wavefront (16 lanes for 8-byte
-    elements, 8 for 16-byte ones) hit distinct bank groups."""
-    S = max(R, 5)
-    phys = lambda e: e ^ ((e >> S) & 31)
-    group = 128 // elem
-    for regs, thread in _layouts(K, R):
-        for m in range(1 << R):
-            base_m = sum(((m >> i) & 1) << regs[i] for i in range(R))
-            for t0 in range(0, 1 << (K - R), 32):
-                addrs = []
-                for lane in range(32):
-                    t = t0 + lane
-                    e = base_m | sum(((t >> i) & 1) << thread[i] for i in range(K - R))
-                    addrs.append(phys(e))
-                for w in range(0, 32, group):
-                    banks = {a % group for a in addrs[w:w + group]}
-                    assert len(banks) == group, (regs, m, t0)
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_planner_matches_host_mirror(lib, dtype):
+    """The library's tile shapes are exactly those the index-math checks use."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from layout_mirror import CFG, PAGE_BIT, make_shapes
+    key = ("c64" if dtype == 0 else "c128", False)
+    KA, KB, R, cmin = CFG[key]
+    for n in range(1, 35 if dtype == 0 else 31):
+        got = qs.plan_shapes(n, dtype)
+        want = make_shapes(max(n, 13), KA, KB, cmin, PAGE_BIT[key[0]])
+        assert [(s["kind"], s["K"], s["c"]) for s in got] == [(s["kind"], s["K"], s["c"]) for s in want], n
+        for g, w in zip(got, want):
+            if w["kind"] == 1:
+                assert (g["g0"], g["n1"], g["g1"]) == (w["g0"], w["n1"], w["g1"]), (n, g, w)

@@ -1,56 +1,19 @@
 """Host-side check of the sweep kernel's index arithmetic (no GPU).
 
-The functions below restate, line for line, the address formulas of the
-sweep kernel (tile_base, gofs, SlotMap, the register layouts) and the planner's
-tile shapes.  For every qubit count and tile shape they must map
-(tile, thread, slot) onto the 2^n amplitudes one-to-one and in bounds, and
-the layout-0 slot offsets must agree with the tile-to-global map used by the
-cost evaluation.  This is the check that keeps a wrong stride from ever
-reaching the GPU as an out-of-bounds access.
+tests/layout_mirror.py restates the tile shapes, the register layouts and
+the address formulas of the CUDA sweep.  For every qubit count and shape they
+must map (tile, thread, slot) onto the 2^n amplitudes one-to-one and in
+bounds; layout 0's slot offsets (the coalesced stores) must agree with the
+tile-to-global map (the TMA box and the cost evaluation); the layouts must
+rotate every target exactly once; and the shared-memory swizzle must be
+conflict-free in every layout.  This keeps a wrong stride from ever reaching
+the GPU as an out-of-bounds access.
 """
 import numpy as np
 import pytest
 
-CFG = {("c64", False): (12, 13, 6, 2), ("c64", True): (12, 13, 5, 2),
-       ("c128", False): (11, 12, 5, 2), ("c128", True): (11, 12, 4, 2)}
-
-
-def make_shapes(nphys, KA, KB, R, cmin):
-    shapes = [(KA, 0, 0, KA)]
-    g = KA
-    while g < nphys:
-        nt = min(KB - cmin, nphys - g)
-        shapes.append((KB, KB - nt, g, nt))
-        g += nt
-    return shapes
-
-
-def gofs(e, c, g0):
-    return (e & ((1 << c) - 1)) | ((e >> c) << g0)
-
-
-def tile_base(t, c, g0, K):
-    mid = g0 - c
-    midm = (1 << mid) - 1 if mid > 0 else 0
-    return ((t & midm) << c) | ((t >> mid) << (g0 + K - c))
-
-
-def slot_off(m, K, R, c, g0):
-    lo = K - R
-    cs = c - lo if c > lo else 0
-    sh = g0 if cs else g0 + lo - c
-    if cs == 0:
-        return m << sh
-    return ((m & ((1 << cs) - 1)) << lo) | ((m >> cs) << sh)
-
-
-def e_thread(tid, lo, R):
-    return (tid & ((1 << lo) - 1)) | ((tid >> lo) << (lo + R))
-
-
-def layouts(K, R):
-    G = -(-K // R)
-    return [max(K - (g + 1) * R, 0) for g in range(G)]
+from layout_mirror import (CFG, MIN_PHYS, PAGE_BIT, e_slot, e_thread, make_layout, make_shapes, phys, rank_of,
+                           slot_off0, tile_base, tile_to_global)
 
 
 @pytest.mark.parametrize("key", list(CFG))
@@ -58,36 +21,74 @@ def test_every_sweep_is_a_bijection(key):
     KA, KB, R, cmin = CFG[key]
     nmax = 34 if key[0] == "c64" else 30
     for n in range(1, nmax + 1):
-        nphys = max(n, 12)
-        shapes = make_shapes(nphys, KA, KB, R, cmin)
-        covered = 0
-        for K, c, g0, nt in shapes:
-            assert 0 <= c <= K and c <= g0 and g0 + nt <= nphys and K - c == nt
-            assert K - R >= 5
-            covered += nt
+        nphys = max(n, MIN_PHYS)
+        page = PAGE_BIT[key[0]]
+        shapes = make_shapes(nphys, KA, KB, cmin, page)
+        assert sum(s["nt"] for s in shapes) == nphys
+        # every qubit is a target of exactly one shape
+        gbit = lambda tb, sh: tile_to_global(1 << tb, sh).bit_length() - 1
+        owned = []
+        for sh in shapes:
+            owned += [gbit(tb, sh) for tb in range(sh["K"] - 1 if sh["kind"] == 0 else sh["K"])
+                      if sh["kind"] == 0 or tb >= sh["c"]]
+        assert sorted(owned) == list(range(nphys))
+        if nphys >= 34 and key[0] == "c64":
+            # the page footprint of the strided tiles is balanced: 2^8 pages each
+            assert max(sum(1 for tb in range(sh["c"], sh["K"]) if gbit(tb, sh) >= page)
+                       for sh in shapes[1:]) == 8
+        for sh in shapes:
+            K, c, g0, nt = sh["K"], sh["c"], sh["g0"], sh["nt"]
+            assert K - R >= 5 and K <= nphys
+            if sh["kind"] == 1:
+                assert 0 <= c <= K and c <= g0 and K - c == nt and 0 <= sh["n1"] <= nt
+                assert sh["g1"] + nt - sh["n1"] <= nphys and (sh["n1"] == 0 or sh["g0"] + sh["n1"] <= sh["g1"])
+            lays = make_layout(K, R, sh["kind"])
             ntiles = 1 << (nphys - K)
             NT, NS = 1 << (K - R), 1 << R
-            offs = np.array([slot_off(m, K, R, c, g0) for m in range(NS)], dtype=np.int64)
-            # layout 0 slot offsets == tile-to-global map of the register tile bits
-            assert all(offs[m] == gofs(m << (K - R), c, g0) for m in range(NS))
-            thr = np.array([gofs(t, c, g0) for t in range(NT)], dtype=np.int64)
+            offs = np.array([slot_off0(m, sh, R, lays[0]) for m in range(NS)], dtype=np.int64)
+            assert all(offs[m] == tile_to_global(e_slot(m, lays[0]), sh) for m in range(NS))
+            thr = np.array([tile_to_global(e_thread(t, lays[0]), sh) for t in range(NT)], dtype=np.int64)
             in_tile = (thr[:, None] + offs[None, :]).ravel()
-            if nphys <= 22:
-                tiles = np.array([tile_base(t, c, g0, K) for t in range(ntiles)], dtype=np.int64)
+            assert np.unique(in_tile).size == 1 << K
+            if nphys <= 21:
+                tiles = np.array([tile_base(t, sh) for t in range(ntiles)], dtype=np.int64)
                 allidx = (tiles[:, None] + in_tile[None, :]).ravel()
                 assert allidx.min() == 0 and allidx.max() == (1 << nphys) - 1
                 assert np.unique(allidx).size == 1 << nphys
             else:
-                # in-tile offsets and tile bases occupy disjoint bits
                 tmask = 0
-                for t in range(ntiles.bit_length()):
-                    tmask |= tile_base(1 << t, c, g0, K) if (1 << t) < ntiles else 0
+                for b in range(nphys - K):
+                    tmask |= tile_base(1 << b, sh)
                 imask = int(np.bitwise_or.reduce(in_tile))
                 assert tmask & imask == 0 and (tmask | imask) == (1 << nphys) - 1
-                assert np.unique(in_tile).size == 1 << K
-            # every layout: thread part and slot part are disjoint tile bits
-            for lo in layouts(K, R):
-                regs = sum(1 << (lo + b) for b in range(R))
-                tparts = {e_thread(t, lo, R) for t in range(NT)}
-                assert all(tp & regs == 0 and tp < (1 << K) for tp in tparts) and len(tparts) == NT
-        assert covered == nphys
+            # every target rotated exactly once per round, carried bits never
+            targets = set(range(K - 1)) if sh["kind"] == 0 else set(range(c, K))
+            rotated = []
+            for lay in lays:
+                lo, hi = lay["rot"]
+                rotated += [b for b in lay["regs"] if lo <= rank_of(K, sh["kind"], b) < hi and b in targets]
+            assert sorted(rotated) == sorted(targets)
+            for lay in lays:
+                tp = {e_thread(t, lay) for t in range(NT)}
+                regs = sum(1 << b for b in lay["regs"])
+                assert len(tp) == NT and all(x & regs == 0 and x < (1 << K) for x in tp)
+
+
+@pytest.mark.parametrize("key", list(CFG))
+def test_swizzle_is_conflict_free(key):
+    """For every layout, slot and warp the lanes of each shared-memory
+    wavefront (16 lanes for 8-byte elements, 8 for 16-byte ones) hit distinct
+    bank groups; dense layout-0 accesses (TMA landing buffer) too."""
+    KA, KB, R, _ = CFG[key]
+    group = 16 if key[0] == "c64" else 8
+    for K, kind in ((KA, 0), (KB, 1)):
+        lays = make_layout(K, R, kind)
+        for li, lay in enumerate(lays):
+            for m in range(1 << R):
+                for t0 in range(0, 1 << (K - R), 32):
+                    for sw in (True, False) if li == 0 else (True,):
+                        addrs = [(phys if sw else (lambda e, r: e))(e_thread(t0 + l, lay) | e_slot(m, lay), R)
+                                 for l in range(32)]
+                        for w in range(0, 32, group):
+                            assert len({a % group for a in addrs[w:w + group]}) == group, (key, kind, li, m)
+
