@@ -138,6 +138,30 @@ int qs_readout(qs_handle h, double* E, double* P, double* norm);
 int qs_cost_info(qs_handle h, int64_t* cmin, int64_t* cmax, int64_t* argmin, int64_t* ground_count,
                  int* scale_shift);
 
+/* Allocation-free variant of the ground-state enumeration behind
+ * qs_set_ising / qs_cost_info.  The paper has no counterpart: it serves
+ * callers that cannot allocate device memory.
+ *   n, hfield, n_edges, edges, J   as for qs_set_ising (same validation);
+ *                                  n at most QS_NOALLOC_MAX_QUBITS.
+ *   cuda_stream  cudaStream_t to run on; NULL = the legacy default stream.
+ *   outputs      as for qs_cost_info (any may be NULL); written on success.
+ * It calls no cudaMalloc, cudaFree or other allocating routine and needs no
+ * handle: its scratch (cost program, per-block partials, result words) is a
+ * file-scope device array of QS_NOALLOC_SCRATCH_BYTES bytes, whose address
+ * is looked up once per device (with that device current) on the first call
+ * there; make that first call before any stream capture begins.  Every call
+ * in the process shares that array, so calls that overlap on the GPU (from
+ * several host threads or streams) race.  Nothing in it has to start at
+ * zero: a call writes each word before reading it.  Inputs beyond the limits
+ * (or a cost program longer than the scratch holds) give QS_EINVAL with the
+ * reason.  Synchronises the stream.  Errors: QS_EINVAL, QS_ENOTINT,
+ * QS_ECUDA. */
+#define QS_NOALLOC_MAX_QUBITS 40
+#define QS_NOALLOC_SCRATCH_BYTES 99584
+int qs_enumerate_noalloc(int n, const double* hfield, int n_edges, const int32_t* edges, const double* J,
+                         void* cuda_stream, int64_t* cmin, int64_t* cmax, int64_t* argmin, int64_t* ground_count,
+                         int* scale_shift);
+
 /* Gradient of F = <psi_p|O|psi_p> with respect to all 2p angles, where O is
  * H_C (QS_OBJ_ENERGY) or the projector on the minimal-cost states
  * (QS_OBJ_GROUND).  Not in the paper: reverse-mode through the unitary layers,

@@ -2,9 +2,13 @@
 // reductions, the full-enumeration ground-state search, the plain per-gate
 // path, and the on-device Adam update.
 #include <atomic>
+#include <cmath>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
+#include "../../include/qs.h"
+#include "qs_api_common.h"
 #include "qs_internal.h"
 
 namespace qs {
@@ -497,4 +501,190 @@ cudaError_t launch_gather_grad(const double* dsrc, double* ddst, int64_t count, 
     return note_launch(cudaGetLastError());
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free ground-state enumeration.
+//
+// The same enumeration kernels as above, with their scratch (the cost
+// program, the per-block partials and the four result words) in one
+// file-scope device array instead of memory from cudaMalloc, for callers
+// that cannot allocate device memory.  The array is shared by every call in
+// the process: calls that overlap on the GPU (concurrent host threads, or
+// several streams) race on it.  No word of it has to start at zero: a call
+// writes the cost program, every partial slot it reads and the result words
+// before reading them.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNaMaxBlocks = 2048;                         // partial slots (4 int64 each)
+constexpr int kNaProgWords = 8448;                         // int32 words of cost program
+constexpr size_t kNaPartOff = 256;                         // bytes; result words at 0
+constexpr size_t kNaProgOff = kNaPartOff + (size_t)kNaMaxBlocks * 4 * sizeof(int64_t);
+constexpr size_t kNaBytes = kNaProgOff + (size_t)kNaProgWords * sizeof(int32_t);
+static_assert(kNaBytes == QS_NOALLOC_SCRATCH_BYTES, "scratch size disagrees with qs.h");
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+int na_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "qs_enumerate_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNaMaxDevices) return set_error(QS_EINVAL, "qs_enumerate_noalloc: device %d >= %d", dev, kNaMaxDevices);
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "qs_enumerate_noalloc: cudaGetSymbolAddress");
+        g_na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_na_ptr[dev];
+    return QS_OK;
+}
+
+}  // namespace
+
 }  // namespace qs
+
+using namespace qs;
+
+extern "C" int qs_enumerate_noalloc(int n, const double* hfield, int n_edges, const int32_t* edges, const double* J,
+                                    void* cuda_stream, int64_t* cmin, int64_t* cmax, int64_t* argmin,
+                                    int64_t* ground_count, int* scale_shift) {
+    // Validation: the rules of qs_set_ising, checked without host allocation.
+    if (n < 1 || n > QS_NOALLOC_MAX_QUBITS)
+        return set_error(QS_EINVAL, "qs_enumerate_noalloc: n = %d outside [1, %d]", n, QS_NOALLOC_MAX_QUBITS);
+    if (n_edges < 0 || n_edges > QS_MAX_EDGES)
+        return set_error(QS_EINVAL, "qs_enumerate_noalloc: n_edges = %d outside [0, %d]", n_edges, QS_MAX_EDGES);
+    if (!hfield) return set_error(QS_EINVAL, "qs_enumerate_noalloc: hfield is NULL");
+    if (n_edges > 0 && (!edges || !J)) return set_error(QS_EINVAL, "qs_enumerate_noalloc: edges or J is NULL");
+    uint64_t seen[QS_NOALLOC_MAX_QUBITS] = {};
+    for (int e = 0; e < n_edges; ++e) {
+        const int i = edges[2 * e], j = edges[2 * e + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n) return set_error(QS_EINVAL, "qs_enumerate_noalloc: edge %d out of range", e);
+        if (i >= j) return set_error(QS_EINVAL, "qs_enumerate_noalloc: edge %d does not satisfy i < j", e);
+        if ((seen[i] >> j) & 1) return set_error(QS_EINVAL, "qs_enumerate_noalloc: duplicate edge %d", e);
+        seen[i] |= 1ull << j;
+        if (!std::isfinite(J[e])) return set_error(QS_EINVAL, "qs_enumerate_noalloc: non-finite coupling %d", e);
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(hfield[i])) return set_error(QS_EINVAL, "qs_enumerate_noalloc: non-finite field %d", i);
+    int shift = -1;
+    for (int s = 0; s <= 3 && shift < 0; ++s) {
+        const double sc = std::ldexp(1.0, s);
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) ok = std::nearbyint(hfield[i] * sc) == hfield[i] * sc;
+        for (int e = 0; e < n_edges && ok; ++e) ok = std::nearbyint(J[e] * sc) == J[e] * sc;
+        if (ok) shift = s;
+    }
+    if (shift < 0) return set_error(QS_ENOTINT, "qs_enumerate_noalloc: weights are not integer multiples of 2^-s, s <= 3");
+    const double sc = std::ldexp(1.0, shift);
+    double bound = 0;
+    for (int i = 0; i < n; ++i) bound += std::fabs(hfield[i] * sc);
+    for (int e = 0; e < n_edges; ++e) bound += std::fabs(J[e] * sc);
+    if (bound > (double)(1 << 24)) return set_error(QS_ENOTINT, "qs_enumerate_noalloc: cost range exceeds 2^24 units");
+    auto hi = [&](int i) { return (int32_t)(hfield[i] * sc); };
+    auto Ji = [&](int e) { return (int32_t)(J[e] * sc); };
+
+    // Cost program with register qubits 0..5 (the layout enum_eval_all reads):
+    // header, outside fields, outside couplings, per-register field and
+    // coupling lists, and the 64-entry table of register-register couplings.
+    int32_t prog[kNaProgWords];
+    int len = 12;
+    auto push = [&](int32_t v) {
+        if (len < kNaProgWords) prog[len] = v;
+        ++len;
+    };
+    const int nreg = n < 6 ? n : 6;
+    for (int b = 0; b < 12; ++b) prog[b] = 0;
+    prog[0] = 6;
+    for (int b = 0; b < 6; ++b) prog[5 + b] = b < nreg ? b : -1;
+    int64_t const0 = 0;
+    int nf = 0, ne = 0;
+    for (int i = nreg; i < n; ++i) {
+        if (hi(i) == 0) continue;
+        push(i);
+        push(hi(i));
+        const0 += hi(i);
+        ++nf;
+    }
+    for (int e = 0; e < n_edges; ++e) {
+        const int i = edges[2 * e], j = edges[2 * e + 1];
+        if (i < nreg || j < nreg || Ji(e) == 0) continue;
+        push(i | (j << 8));
+        push(Ji(e));
+        const0 += Ji(e);
+        ++ne;
+    }
+    for (int b = 0; b < 6; ++b) {
+        if (b >= nreg) {
+            push(0);
+            push(0);
+            continue;
+        }
+        int64_t fb0 = hi(b);
+        int cnt = 0;
+        for (int e = 0; e < n_edges; ++e) {
+            const int i = edges[2 * e], j = edges[2 * e + 1];
+            if ((i == b && j >= nreg) || (j == b && i >= nreg)) cnt += Ji(e) != 0;
+        }
+        const int at = len;
+        push(0);
+        push(cnt);
+        for (int e = 0; e < n_edges; ++e) {
+            const int i = edges[2 * e], j = edges[2 * e + 1];
+            int other = -1;
+            if (i == b && j >= nreg) other = j;
+            else if (j == b && i >= nreg) other = i;
+            if (other < 0 || Ji(e) == 0) continue;
+            fb0 += Ji(e);
+            push(other);
+            push(Ji(e));
+        }
+        if (at < kNaProgWords) prog[at] = (int32_t)fb0;
+    }
+    const int qoff = len;
+    for (int m = 0; m < 64; ++m) {
+        int64_t q = 0;
+        for (int e = 0; e < n_edges; ++e) {
+            const int i = edges[2 * e], j = edges[2 * e + 1];
+            if (i >= nreg || j >= nreg) continue;
+            q += (int64_t)Ji(e) * (((m >> i) & 1) ? -1 : 1) * (((m >> j) & 1) ? -1 : 1);
+        }
+        push((int32_t)q);
+    }
+    if (len > kNaProgWords)
+        return set_error(QS_EINVAL, "qs_enumerate_noalloc: cost program needs %d words, the scratch holds %d", len,
+                         kNaProgWords);
+    prog[1] = nf;
+    prog[2] = ne;
+    prog[3] = (int32_t)const0;
+    prog[4] = qoff;
+
+    unsigned char* base = nullptr;
+    if (int rc = na_scratch(&base)) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int32_t* dprog = reinterpret_cast<int32_t*>(base + kNaProgOff);
+    int64_t* dpart = reinterpret_cast<int64_t*>(base + kNaPartOff);
+    int64_t* dout = reinterpret_cast<int64_t*>(base);
+    // pageable source: the copy has been staged when cudaMemcpyAsync returns
+    cudaError_t e = cudaMemcpyAsync(dprog, prog, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_enumerate_noalloc: program upload");
+    e = launch_enumerate(dprog, n, dpart, (int64_t)kNaMaxBlocks * 4, dout, st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_enumerate_noalloc: enumerate launch");
+    int64_t res[4];
+    e = cudaMemcpyAsync(res, dout, sizeof res, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_enumerate_noalloc: enumerate");
+    if (cmin) *cmin = res[0];
+    if (cmax) *cmax = res[1];
+    if (argmin) *argmin = res[2];
+    if (ground_count) *ground_count = res[3];
+    if (scale_shift) *scale_shift = shift;
+    return QS_OK;
+}

@@ -54,6 +54,7 @@ _SIGS = {
     "qs_ground_prob": [_P, _PD, _PI64, _PI64, _PI64],
     "qs_readout": [_P, _PD, _PD, _PD],
     "qs_cost_info": [_P, _PI64, _PI64, _PI64, _PI64, _PI],
+    "qs_enumerate_noalloc": [_I, _PD, _I, _PI32, _PD, _P, _PI64, _PI64, _PI64, _PI64, _PI],
     "qs_grad": [_P, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "qs_set_adjoint_buffer": [_P, _P, ctypes.c_size_t],
     "qs_copy_state": [_P, _P, ctypes.c_size_t],
@@ -237,6 +238,20 @@ class State:
         s, w = ctypes.c_int(), ctypes.c_int()
         _check(lib().qs_plan_info(self._h, int(p), ctypes.byref(s), ctypes.byref(w)))
         return s.value, w.value
+
+
+def enumerate_noalloc(h, edges, J, cuda_stream=None):
+    """qs_enumerate_noalloc: (cmin, cmax, argmin, ground_count, shift) of the
+    Ising cost, computed with the library's static device scratch."""
+    h = _f64(h)
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    J = _f64(J)
+    vals = [ctypes.c_int64() for _ in range(4)]
+    s = ctypes.c_int()
+    _check(lib().qs_enumerate_noalloc(int(h.size), _dptr(h), int(e.shape[0]), e.ctypes.data_as(_PI32), _dptr(J),
+                                      _stream_ptr(cuda_stream),
+                                      *[ctypes.byref(v) for v in vals], ctypes.byref(s)))
+    return tuple(v.value for v in vals) + (s.value,)
 
 
 def plan_sweeps(n: int, p: int, dtype: int = QS_C64):
