@@ -88,21 +88,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(n: int = 22, layers: int = 1, seed_cfg: int = 5):
-    """Time the CPU oracle on one seeded ER(4) instance of the workload family:
-    `layers` gate-by-gate complex128 layers at n qubits.  Returns
-    (amplitude-updates/s, seconds, threads)."""
+def oracle_sample(n: int = 26, layers: int = 1, seed_cfg: int = 5, target_s: float = 0.0):
+    """Time the CPU oracle on one seeded ER(4) instance of the workload family
+    (h, J in U{-1,0,1}, AQA angles tau = 0.75): gate-by-gate complex128 layers
+    at n qubits and the readout.  With target_s > 0 the layer count is chosen
+    from a one-layer probe so the timed sample takes about target_s seconds.
+    Returns (amplitude-updates/s, seconds, threads, layers)."""
     import numpy as np
     import oracle
     from paper_2104_03293_gb300 import instances as I
     inst = I.erdos_renyi_ising(n, I.workload_seed(seed_cfg, 0), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
-    s = np.arange(1, layers + 1) / (layers + 1)
-    g, b = oracle.aqa_angles(0.75, s)
-    t0 = time.perf_counter()
-    psi = oracle.evolve(inst, g, b)
-    oracle.readout(inst, psi, cmin=0.0)
-    dt = time.perf_counter() - t0
-    return layers * (n + 1) * 2.0 ** n / dt, dt, oracle.num_threads()
+
+    def run(L):
+        s = np.arange(1, L + 1) / (L + 1)
+        g, b = oracle.aqa_angles(0.75, s)
+        t0 = time.perf_counter()
+        psi = oracle.evolve(inst, g, b)
+        oracle.readout(inst, psi, cmin=0.0)
+        return time.perf_counter() - t0
+
+    if target_s > 0:
+        t1 = run(1)
+        layers = max(1, min(64, int(round(target_s / max(t1, 1e-3)))))
+    dt = run(layers)
+    return layers * (n + 1) * 2.0 ** n / dt, dt, oracle.num_threads(), layers
+
+
+def profiled_traffic():
+    """DRAM bytes per sweep launch (read + write) of the n=34 forward evolve,
+    from the committed ncu launch list, or None when the CUDA sources have
+    changed since that capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_n34_aqa_p20_launch_list.md")
+    try:
+        txt = open(path).read()
+        traffic = int(re.search(r"^traffic_per_launch_bytes: (\d+)$", txt, re.M).group(1))
+        want = re.search(r"^sources_sha256: ([0-9a-f]+)$", txt, re.M).group(1)
+    except Exception:
+        return None
+    d = os.path.join(ROOT, "paper_2104_03293_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return traffic if h.hexdigest() == want else None
+
+
+def workload_config(args):
+    return {"workload": f"AQA n={args.n} p={args.p} tau={args.tau} forward + readout (ER(4) Ising, h,J in "
+                        f"U{{-1,0,1}}); grad of P_ground at n={args.grad_n} wrt tau and {args.p} knots",
+            "n": args.n, "p": args.p, "grad_n": args.grad_n,
+            "l2": f"inputs larger than L2 ({8 * 2 ** args.n / 1e9:.1f} GB state)"}
 
 
 def run_reference(args, rank):
@@ -115,17 +153,16 @@ def run_reference(args, rank):
     vals, secs = [], []
     threads = 1
     for _ in range(args.steps):
-        v, dt, threads = oracle_sample(args.ref_n, 1)
+        v, dt, threads, _ = oracle_sample(args.ref_n, 1)
         vals.append(v)
         secs.append(dt)
     value = sum(vals) / len(vals)
-    sample = (f"one gate-by-gate complex128 AQA layer at n={args.ref_n} (ER(4), h,J in U{{-1,0,1}}) per step; "
-              f"the n=34 state (275 GB in complex128) does not fit the host")
+    sample = (f"one gate-by-gate complex128 AQA layer + readout at n={args.ref_n} (ER(4), h,J in U{{-1,0,1}}) "
+              f"per step; the n={args.n} state ({16 * 2 ** args.n / 1e9:.0f} GB in complex128) does not fit host memory")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": "config 5a sample: AQA layer, ER(4) integer Ising",
-                                            "n": args.ref_n, "p": 1},
+            "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -142,7 +179,7 @@ def main():
     ap.add_argument("--p", type=int, default=20)
     ap.add_argument("--tau", type=float, default=0.75)
     ap.add_argument("--grad-n", type=int, default=33)
-    ap.add_argument("--ref-n", type=int, default=22)
+    ap.add_argument("--ref-n", type=int, default=26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -239,6 +276,7 @@ def main():
     evolve_ms = statistics.mean(timing["evolve_ms"])
     alg_bytes = (16.0 * sweeps - 8.0) * N          # first sweep only writes
     achieved = alg_bytes / (evolve_ms / 1000.0) / 1e9
+    traffic = profiled_traffic() if (n, p) == (34, 20) else None
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     grad_fe = statistics.mean(timing["grad_ms"]) / statistics.mean(timing["fwd2_ms"])
@@ -247,24 +285,23 @@ def main():
     d2h = 3 * 8
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v_cpu, dt_cpu, thr = oracle_sample(args.ref_n, 1)
+        v_cpu, dt_cpu, thr, L = oracle_sample(args.ref_n, target_s=12.0)
         cpu = {"value": v_cpu, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"one gate-by-gate complex128 AQA layer at n={args.ref_n} ({dt_cpu:.1f} s)"}
+               "sample": f"{L} gate-by-gate complex128 AQA layers + readout at n={args.ref_n}, ER(4) "
+                         f"h,J in U{{-1,0,1}} ({dt_cpu:.1f} s); the n={n} state does not fit host memory"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": f"config 5: AQA n={n} p={p} tau={tau} forward + readout; "
-                               f"grad of P_ground at n={n2} wrt tau and {p} knots",
-                   "n": n, "p": p, "grad_n": n2, "l2": "inputs larger than L2 (137 GB state)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": dict(workload_config(args), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "layer_ms": evolve_ms / p,
         "sweeps_per_evolve": sweeps,
         "grad_forward_equivalents": grad_fe,
         "fd_forward_equivalents": 4 * p,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "sweep_kernel (average over the evolve's sweeps)",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes / sweeps,
+                     "kernel": "sweep_kernel (per launch, averaged over the evolve's sweeps)",
                      "peak_source": "measured" if peaks else "fallback"},
         "cpu_baseline": cpu,
         "e2e": {"value": updates / args.steps / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

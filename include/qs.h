@@ -55,7 +55,7 @@ enum qs_status {
     QS_EINVAL = 1,    /* bad argument (size, index, pointer, non-finite angle)    */
     QS_ENOMEM = 2,    /* device allocation failed or caller buffer too small      */
     QS_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error)  */
-    QS_ETIMEOUT = 4,  /* a bounded device-side wait gave up (batched queue)       */
+    QS_ETIMEOUT = 4,  /* a bounded device-side wait gave up (tile load, queue)    */
     QS_ENOTINT = 5,   /* weights are not integer multiples of 2^-s, s <= 3        */
     QS_ESTATE = 6     /* call out of order (e.g. evolve before set_ising)         */
 };
@@ -80,9 +80,9 @@ enum qs_path { QS_PATH_TILED = 0, QS_PATH_PLAIN = 1 };
  *   cuda_stream cudaStream_t to order all work on; NULL = the legacy default
  *               stream.  The caller keeps it alive for the handle's lifetime.
  *   device_buf  optional caller-owned device buffer for the state (for
- *               example a torch tensor), >= 2^max(n, 12) * element bytes,
+ *               example a torch tensor), >= 2^max(n, 13) * element bytes,
  *               256-byte aligned.  NULL: the library allocates and frees it.
- *               States with n < 12 are stored with 12 - n extra idle qubits
+ *               States with n < 13 are stored with 13 - n extra idle qubits
  *               (no cost terms, left in |+>), which changes no readout.
  *   buf_bytes   size of device_buf in bytes (ignored when it is NULL).
  * Errors: QS_EINVAL (n, dtype, alignment), QS_ENOMEM (buffer too small or

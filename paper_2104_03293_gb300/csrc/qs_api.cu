@@ -322,8 +322,7 @@ static int prepare_layers(qs_handle h, int p, const double* gamma, const double*
 }
 
 static SweepTask make_task(qs_handle h, const Shape& sh, const PlanSweep& ps, int cfgi, int shape_idx, void* lam,
-                           const LayerDev* layers, const void* tab, int p, double* partials, int objective,
-                           int* map_err) {
+                           const LayerDev* layers, const void* tab, int p, double* partials, int objective) {
     Instance& I = h->inst;
     SweepTask t;
     std::memset(&t, 0, sizeof t);
@@ -351,12 +350,11 @@ static SweepTask make_task(qs_handle h, const Shape& sh, const PlanSweep& ps, in
     t.kind = sh.kind;
     t.n1 = sh.n1;
     t.g1 = sh.g1;
-    (void)map_err;
     return t;
 }
 
-// Blob uploaded once per call: tasks, per-launch tile prefixes, reduce tasks.
-// 64-byte alignment keeps the tensor maps inside the tasks aligned.
+// Blob uploaded once per call: tasks, per-launch tile prefixes, reduce tasks,
+// each record 64-byte aligned.
 struct CallBlob {
     std::vector<unsigned char> bytes;
     size_t add(const void* p, size_t n) {
@@ -391,15 +389,14 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     std::vector<int> red_cnt;
     const LayerDev* lf = reinterpret_cast<const LayerDev*>(h->layers_f.ptr);
     const LayerDev* lr = reinterpret_cast<const LayerDev*>(h->layers_r.ptr);
-    int map_err = 0;
     for (auto& s : fwd) {
-        SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective, &map_err);
+        SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective);
         fwd_off.push_back(blob.add(&t, sizeof t));
         const int64_t pre[2] = {0, shf[s.shape].ntiles};
         fwd_pre.push_back(blob.add(pre, sizeof pre));
     }
     for (auto& s : rev) {
-        SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective, &map_err);
+        SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective);
         rev_off.push_back(blob.add(&t, sizeof t));
         const int64_t pre[2] = {0, sha[s.shape].ntiles};
         rev_pre.push_back(blob.add(pre, sizeof pre));

@@ -38,7 +38,7 @@ struct Wave {
 struct Blob {
     std::vector<unsigned char> b;
     size_t add(const void* p, size_t n) {
-        size_t off = (b.size() + 63) & ~size_t(63);  // keeps tensor maps 64-byte aligned
+        size_t off = (b.size() + 63) & ~size_t(63);  // 64-byte aligned records
         b.resize(off + n);
         if (n) std::memcpy(b.data() + off, p, n);
         return off;

@@ -8,11 +8,12 @@
 //
 // Persistent CTAs (two per SM for the forward sweep) walk over tiles of 2^K
 // amplitudes:
-//   * TMA brings a tile into the CTA's shared-memory tile buffer
-//     (cp.async.bulk.tensor boxes for strided tiles, cp.async.bulk for
-//     contiguous ones; mbarrier completion, bounded waits).  The load of the
-//     next tile is issued as soon as the current one has been read for the
-//     last time, so it overlaps the tile's remaining work and the other CTA.
+//   * a tile lands in the CTA's shared-memory tile buffer: one bulk copy
+//     (cp.async.bulk, TMA) for a contiguous tile, per-thread 16-byte
+//     cp.async copies for a strided one (runs of 2^c amplitudes); both
+//     complete on an mbarrier, with bounded waits.  The load of the next tile
+//     is issued as soon as the current one has been read for the last time,
+//     so it overlaps the tile's remaining work and the other CTA.
 //   * each thread holds 2^R amplitudes per array in registers.  A layout
 //     (qs_layout.h) assigns R tile bits to the register slot index; the
 //     rotations of those bits are register butterflies.  Changing layout is a

@@ -21,7 +21,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_ENOTINT, QS_ESTATE = rang
 QS_C64, QS_C128 = 0, 1
 QS_OBJ_ENERGY, QS_OBJ_GROUND = 0, 1
 QS_PATH_TILED, QS_PATH_PLAIN = 0, 1
-MIN_PHYS_QUBITS = 12
+MIN_PHYS_QUBITS = 13
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_ENOTINT",
            6: "QS_ESTATE"}
