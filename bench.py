@@ -136,6 +136,21 @@ def profiled_traffic():
     return traffic if h.hexdigest() == want else None
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job's time); every rank receives the result."""
+    import torch
+    t = torch.tensor(values, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def aggregate_value(units_per_rank, world, seconds):
+    """Whole-job throughput: units processed by all ranks over the slowest
+    rank's time (replicas: every rank does the same work)."""
+    return world * units_per_rank / seconds
+
+
 def workload_config(args):
     return {"workload": f"AQA n={args.n} p={args.p} tau={args.tau} forward + readout (ER(4) Ising, h,J in "
                         f"U{{-1,0,1}}); grad of P_ground at n={args.grad_n} wrt tau and {args.p} knots",
@@ -264,15 +279,13 @@ def main():
     total_ms = ta.elapsed_time(tb)
     evolve_s = sum(timing["evolve_ms"]) / 1000.0
     if dist:
-        t = torch.tensor([total_ms, evolve_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, evolve_s = float(t[0]), float(t[1])
+        total_ms, evolve_s = max_over_ranks([total_ms, evolve_s], dist, "cuda")
     if rank != 0:
         dist.destroy_process_group()
         return 0
 
     updates = args.steps * p * (n + 1) * float(N)
-    value = world * updates / evolve_s
+    value = aggregate_value(updates, world, evolve_s)
     evolve_ms = statistics.mean(timing["evolve_ms"])
     alg_bytes = (16.0 * sweeps - 8.0) * N          # first sweep only writes
     achieved = alg_bytes / (evolve_ms / 1000.0) / 1e9
