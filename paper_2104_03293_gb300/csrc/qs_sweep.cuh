@@ -40,6 +40,7 @@ template <> struct C2T<double> { using T = double2; };
 
 template <class Real> __device__ __forceinline__ Real fma_(Real a, Real b, Real c) { return fma(a, b, c); }
 
+
 // Compile-time loop: f(std::integral_constant<int, I>) for I in [Begin, End).
 template <int I, int End, class F>
 __device__ __forceinline__ void static_for(F&& f) {
@@ -560,7 +561,8 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
             if (kPhase && rd.phase_pre) S::phase_any(cur, v, T, tm, base, tid, ltab, ly.frame, gG);
             const Real fabs2 = (Real)(ly.fabs * ly.fabs);
             Real fpow = 1;
-            if (NA == 2) fpow = (Real)pow(ly.fabs, 2.0 * rd.r0);
+            if (NA == 2)
+                for (int i = 0; i < rd.r0; ++i) fpow *= fabs2;  // |f|^{2 r0}, no FP64 on the device
             const Real w = (Real)ly.w;
             if (cur == 0) {
                 for (int g = 0; g < ga; ++g) {
