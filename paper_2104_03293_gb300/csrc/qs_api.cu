@@ -11,6 +11,7 @@
 
 #include "../../include/qs.h"
 #include "qs_api_common.h"
+#include "qs_pair.h"
 
 namespace qs {
 
@@ -127,6 +128,17 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
                 prog_off[cfgi][s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, cfg.R));
             }
     }
+    for (size_t s = 0; s < shapes[0].size(); ++s) {
+        const Shape& sh = shapes[0][s];
+        if (!pair_choice(dtype, 0, sh.kind, sh.c, 1)) continue;
+        const PairLayout PL = pair_layout(sh.c);
+        for (int g = 0; g < 2; ++g) {
+            int regq[6];
+            regq[0] = shape_bit(sh, PL.P);  // slot bit 0: the pack bit; bits 1..5: regs[g]
+            for (int b = 0; b < 5; ++b) regq[1 + b] = shape_bit(sh, PL.regs[g][b]);
+            prog_pair[s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, 6));
+        }
+    }
     {
         int regq[6];
         for (int b = 0; b < 6; ++b) regq[b] = b < n ? b : -1;
@@ -187,7 +199,7 @@ struct qs_state {
     Uploader up, up_ang;
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
-    int grid[2][2] = {{0, 0}, {0, 0}};  // [adjoint][K == K_A ? 0 : 1]
+    int grid[2][4] = {};  // [adjoint][kernel kind; 3 = packed-pair kernel]
     int device = 0;
 };
 
@@ -290,7 +302,7 @@ int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* 
 // Grid size of the persistent sweep kernel for a tile shape.
 static int grid_for(qs_handle h, int kind, int adjoint) {
     int& g = h->grid[adjoint][kind];
-    if (!g) g = sweep_grid(h->dtype, adjoint, kind);
+    if (!g) g = kind == 3 ? sweep_pair_grid() : sweep_grid(h->dtype, adjoint, kind);
     return g;
 }
 
@@ -391,6 +403,9 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     const LayerDev* lr = reinterpret_cast<const LayerDev*>(h->layers_r.ptr);
     for (auto& s : fwd) {
         SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective);
+        const Shape& sh = shf[s.shape];
+        if (pair_choice(h->dtype, 0, sh.kind, sh.c, sweep_variant(s.flags, s.nr, s.r)))
+            for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_pair[s.shape][g < 2 ? g : 0]);
         fwd_off.push_back(blob.add(&t, sizeof t));
         const int64_t pre[2] = {0, shf[s.shape].ntiles};
         fwd_pre.push_back(blob.add(pre, sizeof pre));
@@ -423,19 +438,20 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     }
     for (size_t i = 0; i < fwd.size(); ++i) {
         const Shape& sh = shf[fwd[i].shape];
-        SweepLaunch L{sh.kind, sweep_variant(fwd[i].flags, fwd[i].nr, fwd[i].r), 0, h->dtype, 1, sh.ntiles,
+        SweepLaunch L{kernel_kind(sh), sweep_variant(fwd[i].flags, fwd[i].nr, fwd[i].r), 0, h->dtype, 1, sh.ntiles,
                       reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
-        e = launch_sweep(L, grid_for(h, sh.kind, 0), h->st);
+        L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
+        e = launch_sweep(L, L.pairc ? grid_for(h, 3, 0) : grid_for(h, L.kind, 0), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
     }
     e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + rd_off), 1, h->st);
     if (e != cudaSuccess) return cuda_error(e, "readout reduce");
     for (size_t i = 0; i < rev.size(); ++i) {
         const Shape& sh = sha[rev[i].shape];
-        SweepLaunch L{sh.kind, 0, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
+        SweepLaunch L{kernel_kind(sh), 0, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + rev_pre[i]), derr};
-        e = launch_sweep(L, grid_for(h, sh.kind, 1), h->st);
+        e = launch_sweep(L, grid_for(h, L.kind, 1), h->st);
         if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
         if (red_cnt[i]) {
             e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + red_off[i]), red_cnt[i], h->st);

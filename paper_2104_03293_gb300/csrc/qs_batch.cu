@@ -67,7 +67,7 @@ struct qs_batch {
     std::vector<Wave> fwd_waves, rev_waves;
     size_t prep_f_off = 0, prep_r_off = 0;
     bool plan_grad = false, planned = false;
-    int grid[2][2] = {{0, 0}, {0, 0}};
+    int grid[2][3] = {};  // [adjoint][kernel kind]
     cudaGraphExec_t graph = nullptr;
     bool have_results = false;
     int objective = 0;
@@ -214,7 +214,7 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
             Wave wave;
             int64_t pbase = 0;
             std::vector<ReduceTask> rts;
-            for (int kind = 0; kind < 2; ++kind) {
+            for (int kind = 0; kind < 3; ++kind) {
                 std::vector<SweepTask> tasks;
                 std::vector<int64_t> pre{0};
                 int variant = 2;  // leanest kernel that serves every task of the launch
@@ -223,7 +223,7 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
                     const PlanSweep& s = L[i][w];
                     const Instance& I = b->inst[i];
                     const Shape& sh = I.shapes[adj][s.shape];
-                    if (sh.kind != kind) continue;
+                    if (kernel_kind(sh) != kind) continue;
                     variant = std::min(variant, sweep_variant(s.flags, s.nr, s.r));
                     SweepTask t;
                     std::memset(&t, 0, sizeof t);

@@ -26,6 +26,7 @@ constexpr int kMinPhysQubits = 13;   // states with n < 13 are padded with idle 
 constexpr int kMaxRounds = 8;        // rounds (layers) fused into one sweep
 constexpr int kMaxShapes = 4;        // tile shapes per plan
 constexpr int kMaxLayouts = 3;       // register layouts per tile shape
+constexpr int kRunBits = 8;          // run-structured shape A: runs of 2^8 amplitudes
 #define QS_MAX_LAYERS_PREP 1024          // layers per preparation call
 
 // Register-layout parameters per kernel configuration.
@@ -95,6 +96,7 @@ struct SweepLaunch {
     const int64_t* tile_prefix;    // device, ntasks + 1
     int* err;                      // device error word (set on a timed-out wait)
     int group = 1;                 // consecutive tiles per CTA turn (a power of 2)
+    int pairc = 0;                 // 2 or 3: packed-pair kernel for carried bits c (qs_pair.h)
 };
 
 // Cost program: the Ising cost of Eq. (HC) specialised to one register layout.
@@ -108,6 +110,11 @@ std::vector<int32_t> build_cost_prog(int n, const std::vector<int32_t>& h, const
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All return cudaError_t.
+cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st);
+int sweep_pair_grid();
+// Packed-pair kernel choice for a sweep: the carried-bit count c when the
+// strided complex64 forward sweep without readout can use it, else 0.
+int pair_choice(int dtype, int adjoint, int kind, int c, int variant);
 // ---------------------------------------------------------------------------
 // Launch accounting (qs_launch_count): every launcher reports its kernels.
 cudaError_t note_launch(cudaError_t e, int kernels = 1);

@@ -1,0 +1,85 @@
+// Register layouts of the packed-pair sweep: strided complex64 tiles (kind 1,
+// K = 13 tile bits, c = 2 or 3 carried low bits), forward rotations and phase.
+//
+// A thread holds 64 amplitudes as 32 pairs.  The two amplitudes of a pair
+// differ in the pack bit P = c (the lowest target bit) and are stored split
+// by component, X = (re_a, re_b) and Y = (im_a, im_b), so one packed f32x2
+// FMA updates both: a butterfly on any other register bit costs four f32x2
+// FMAs per four amplitudes instead of eight scalar FMAs.  The rotation of the
+// pack bit itself mixes the two halves of a pair and is done with scalar FMAs.
+//
+// Layout g puts the pack bit and the five tile bits regs[g][0..4] into the
+// registers (pair index j: bit b <-> regs[g][b]) and the seven tbits[g] into
+// the thread index (tbits[g][0..4] are the lane bits).  Layout 0 holds the
+// five top tile bits, so its stores are coalesced over the carried bits;
+// layout 1 holds the remaining targets.  Both layouts hold the pack bit, which
+// layout 0 rotates.  The shared-memory transposes move 16-byte pairs (X, Y);
+// the pair unit u is the tile index with the pack bit removed, placed at
+// phys(u) = u ^ fold3(u), where fold3 XORs the 3-bit groups of u above the
+// lowest into it.  The lane order puts on lanes 0..2 three thread bits whose
+// u positions differ mod 3, so every quarter-warp of 16-byte accesses hits
+// eight distinct bank groups (checked on the host by the test-suite).
+#pragma once
+
+#ifdef __CUDACC__
+#define QS_PHD __host__ __device__
+#else
+#define QS_PHD
+#endif
+
+namespace qs {
+
+constexpr int kPairK = 13;
+
+struct PairLayout {
+    int C, P;
+    int regs[2][5];   // tile bit of pair-index bit b (ascending)
+    int tbits[2][7];  // tile bit of thread-index bit t (lane order)
+    int rotmask[2];   // bit b: regs[g][b] is a target rotated in layout g
+};
+
+QS_PHD constexpr bool pair_c_ok(int c) { return c == 2 || c == 3; }
+
+QS_PHD constexpr PairLayout pair_layout(int C) {
+    PairLayout t{};
+    t.C = C;
+    t.P = C;
+    for (int b = 0; b < 5; ++b) t.regs[0][b] = 8 + b;  // top five tile bits
+    if (C == 2) {
+        const int r1[5] = {3, 4, 5, 6, 7};
+        const int t0[7] = {0, 1, 3, 4, 5, 6, 7};
+        const int t1[7] = {0, 1, 9, 8, 10, 11, 12};
+        for (int b = 0; b < 5; ++b) t.regs[1][b] = r1[b];
+        for (int i = 0; i < 7; ++i) {
+            t.tbits[0][i] = t0[i];
+            t.tbits[1][i] = t1[i];
+        }
+        t.rotmask[0] = 0x1f;
+        t.rotmask[1] = 0x1f;
+    } else {
+        // C = 3: targets 3..12; layout 1 rotates 4..7 and holds bit 12 idle
+        const int r1[5] = {4, 5, 6, 7, 12};
+        const int t0[7] = {0, 1, 2, 4, 5, 6, 7};
+        const int t1[7] = {0, 1, 2, 8, 9, 10, 11};
+        for (int b = 0; b < 5; ++b) t.regs[1][b] = r1[b];
+        for (int i = 0; i < 7; ++i) {
+            t.tbits[0][i] = t0[i];
+            t.tbits[1][i] = t1[i];
+        }
+        t.rotmask[0] = 0x1f;
+        t.rotmask[1] = 0x0f;
+    }
+    return t;
+}
+
+// Pair unit of tile element e: e with the pack bit P removed.
+QS_PHD constexpr unsigned pair_unit(unsigned e, int P) {
+    return (e & ((1u << P) - 1u)) | ((e >> (P + 1)) << P);
+}
+
+// Shared-memory position (in 16-byte pairs) of pair unit u; linear in u.
+QS_PHD constexpr unsigned pair_phys(unsigned u) {
+    return u ^ ((u >> 3) & 7u) ^ ((u >> 6) & 7u) ^ ((u >> 9) & 7u);
+}
+
+}  // namespace qs

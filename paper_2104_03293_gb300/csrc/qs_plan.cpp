@@ -151,16 +151,30 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit) {
     Shape a;
     a.K = cfg.K_A; a.c = 0; a.g0 = 0; a.nt = cfg.K_A - 1; a.kind = 0; a.n1 = 0; a.g1 = 0;
     a.ntiles = (int64_t)1 << (nphys - cfg.K_A);
+    // strided shapes cover qubits [lo, hi); bits from `split` up are dealt out
+    int lo = cfg.K_A - 1, hi = nphys, split = page_bit;
+    if (cfg.K_A == 13 && cfg.K_B == 13 && nphys >= 30) {
+        // complex64, largest states: shape A = runs of 2^8 amplitudes (2 KB)
+        // with targets [0, 8) and the top four qubits, batch bit 8; the far
+        // bits left go evenly to the strided shapes
+        const int f = cfg.K_A - 1 - kRunBits;
+        a.c = kRunBits;
+        a.g0 = nphys - f;
+        a.n1 = f;
+        a.g1 = a.c;
+        lo = a.c;
+        hi = nphys - f;
+        split = kFarBitC64;
+    }
     v.push_back(a);
-    const int lo = cfg.K_A - 1;
     const int per = cfg.K_B - cfg.c_min;                   // targets per strided shape
-    const int rest = nphys - lo;
+    const int rest = hi - lo;
     if (rest <= 0) return v;
     const int S = (rest + per - 1) / per;                  // strided shapes
-    const int below = std::max(0, std::min(page_bit, nphys) - lo);  // qubits below the page bit
+    const int below = std::max(0, std::min(split, hi) - lo);  // qubits below the split bit
     const int high = rest - below;
     // water-filling: deal the high qubits one at a time to the shape holding
-    // the fewest, so that the largest page footprint is as small as possible
+    // the fewest, so that the largest far footprint is as small as possible
     std::vector<int> nt(S), nh(S, 0);
     for (int k = 0; k < S; ++k) nt[k] = std::min(per, rest - k * per);
     for (int i = 0; i < high; ++i) {

@@ -20,9 +20,13 @@ struct IsingInt {
 int validate_ising(int n, const double* hfield, int n_edges, const int32_t* edges, const double* J, IsingInt& out,
                    std::string& err);
 
-// A tile shape (see qs_layout.h): kind 0 = 2^K contiguous amplitudes with
-// targets [0, K - 1); kind 1 = c carried low bits + nt = K - c targets in two
-// runs, [g0, g0 + n1) and [g1, g1 + nt - n1) (n1 may be 0).
+// A tile shape (see qs_layout.h).  Tile bits [0, c) are global bits [0, c),
+// tile bits [c, c + n1) global [g0, g0 + n1), the rest global [g1, ...).
+//   kind 0: targets are tile bits [0, K - 1).  Contiguous (c = n1 = g1 = 0),
+//           or runs of 2^c amplitudes whose tile bits [c, K - 1) sit on the
+//           top global bits (g0) and whose batch bit K - 1 is global bit c.
+//   kind 1: c carried low bits (not targets) + nt = K - c targets in the two
+//           runs [g0, g0 + n1) and [g1, g1 + nt - n1) (n1 may be 0).
 struct Shape {
     int K, c, g0, nt, kind, n1, g1;
     int64_t ntiles;
@@ -30,10 +34,19 @@ struct Shape {
 
 // Global bit of tile bit tb of a shape.
 inline int shape_bit(const Shape& s, int tb) {
-    if (s.kind == 0 || tb < s.c) return tb;
+    if (tb < s.c) return tb;
     if (tb < s.c + s.n1) return s.g0 + (tb - s.c);
     return s.g1 + (tb - s.c - s.n1);
 }
+
+// Sweep-kernel kind of a shape: 0 contiguous, 1 strided, 2 kind-0 runs.
+inline int kernel_kind(const Shape& s) { return s.kind == 0 && (s.c != 0 || s.n1 != 0) ? 2 : s.kind; }
+
+// Complex64 index bit from which amplitudes lie 32 MB or more apart: a
+// strided tile with many target bits at or above it streams far slower at
+// 32-byte runs (measured), so the largest states spread those bits over all
+// shapes, including a run-structured shape A.
+constexpr int kFarBitC64 = 22;
 
 struct PlanSweep {
     int shape = 0;

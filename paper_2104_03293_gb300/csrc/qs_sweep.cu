@@ -1,6 +1,7 @@
 // Dispatch of the sweep kernel (templates in qs_sweep.cuh; instantiations in
 // qs_sweep_c64f.cu and qs_sweep_other.cu, compiled in parallel).
 #include "qs_internal.h"
+#include "qs_pair.h"
 
 namespace qs {
 
@@ -14,6 +15,7 @@ cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st) {
     const int64_t groups = L.total_tiles / (L.group > 0 ? L.group : 1);
     if (grid > groups) grid = (int)groups;
     if (grid < 1) grid = 1;
+    if (L.pairc) return launch_sweep_pair(L, grid, st);
     cudaError_t s = cudaErrorInvalidValue;
     if (L.dtype == 0 && !L.adjoint) sweep_c64f(L.kind, L.variant, false, &L, grid, st, &s);
     else sweep_other(L.dtype, L.adjoint, L.kind, false, &L, grid, st, &s);
@@ -23,6 +25,10 @@ cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st) {
 int sweep_grid(int dtype, int adjoint, int kind) {
     if (dtype == 0 && !adjoint) return sweep_c64f(kind, 0, true, nullptr, 0, nullptr, nullptr);
     return sweep_other(dtype, adjoint, kind, true, nullptr, 0, nullptr, nullptr);
+}
+
+int pair_choice(int dtype, int adjoint, int kind, int c, int variant) {
+    return (dtype == 0 && !adjoint && kind == 1 && (c == 2 || c == 3) && variant != 0) ? c : 0;
 }
 
 int sweep_variant(int flags, int nrounds, const SweepRound* rounds) {

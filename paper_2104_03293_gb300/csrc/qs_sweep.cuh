@@ -113,10 +113,12 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 // ---------------------------------------------------------------------------
 // Index maps
 // ---------------------------------------------------------------------------
-// Strided tile map (kind 1): tile bits [0, c) are global bits [0, c); tile
-// bits [c, c + n1) are global [g0, g0 + n1); tile bits [c + n1, K) are global
-// [g1, g1 + K - c - n1).  The non-tile global bits, in ascending order, take
-// the tile index.
+// Tile map: tile bits [0, c) are global bits [0, c); tile bits [c, c + n1)
+// are global [g0, g0 + n1); tile bits [c + n1, K) are global [g1, ...).  The
+// two runs may lie in either order above c.  The non-tile global bits, in
+// ascending order, take the tile index.  A contiguous tile is c = 0, n1 = 0,
+// g1 = 0; other kind-0 tiles are runs of 2^c amplitudes whose higher tile bits
+// lie on distant global bits.
 struct TMap {
     int c, g0, n1, g1, K;
     __device__ __forceinline__ uint64_t gofs(uint32_t e) const {
@@ -124,10 +126,17 @@ struct TMap {
         return (uint64_t)(e & cm) | ((uint64_t)((e >> c) & m1) << g0) | ((uint64_t)(e >> (c + n1)) << g1);
     }
     __device__ __forceinline__ uint64_t base(int64_t t) const {
-        const int la = g0 - c, lb = g1 - (g0 + n1);  // non-tile runs [c, g0), [g0 + n1, g1)
+        // occupied runs above c in ascending global order: [s1, s1 + l1), [s2, s2 + l2)
+        int s1 = g0, l1 = n1, s2 = g1, l2 = K - c - n1;
+        if (l1 == 0) { s1 = s2; l1 = l2; l2 = 0; }
+        if (l2 > 0 && s2 < s1) { const int ts = s1, tl = l1; s1 = s2; l1 = l2; s2 = ts; l2 = tl; }
+        const int la = s1 - c;                        // gap [c, s1)
         const uint64_t u = (uint64_t)t;
-        const uint64_t ma = la > 0 ? (1ull << la) - 1ull : 0ull, mb = lb > 0 ? (1ull << lb) - 1ull : 0ull;
-        return ((u & ma) << c) | (((u >> la) & mb) << (g0 + n1)) | ((u >> (la + lb)) << (g1 + K - c - n1));
+        const uint64_t ma = la > 0 ? (1ull << la) - 1ull : 0ull;
+        if (l2 == 0) return ((u & ma) << c) | ((u >> la) << (s1 + l1));
+        const int lb = s2 - (s1 + l1);                // gap [s1 + l1, s2)
+        const uint64_t mb = lb > 0 ? (1ull << lb) - 1ull : 0ull;
+        return ((u & ma) << c) | (((u >> la) & mb) << (s1 + l1)) | ((u >> (la + lb)) << (s2 + l2));
     }
 };
 
@@ -212,11 +221,13 @@ template <class Real, int K, int R, int NA, int KIND>
 struct Sweep {
     using C2 = typename C2T<Real>::T;
     // layout tables as compile-time scalars (qs_layout.h)
-    static constexpr int G = make_layout(K, R, KIND).G;
-    template <int g, int b> __host__ __device__ static constexpr int reg_bit() { return make_layout(K, R, KIND).regs[g][b]; }
-    template <int g, int j> __host__ __device__ static constexpr int thr_bit() { return make_layout(K, R, KIND).tbits[g][j]; }
-    template <int g> __host__ __device__ static constexpr int rot_lo() { return make_layout(K, R, KIND).rot_lo[g]; }
-    template <int g> __host__ __device__ static constexpr int rot_hi() { return make_layout(K, R, KIND).rot_hi[g]; }
+    // KIND 2 (run-structured kind-0 tiles) uses the kind-0 layouts
+    static constexpr int LK = KIND == 2 ? 0 : KIND;
+    static constexpr int G = make_layout(K, R, LK).G;
+    template <int g, int b> __host__ __device__ static constexpr int reg_bit() { return make_layout(K, R, LK).regs[g][b]; }
+    template <int g, int j> __host__ __device__ static constexpr int thr_bit() { return make_layout(K, R, LK).tbits[g][j]; }
+    template <int g> __host__ __device__ static constexpr int rot_lo() { return make_layout(K, R, LK).rot_lo[g]; }
+    template <int g> __host__ __device__ static constexpr int rot_hi() { return make_layout(K, R, LK).rot_hi[g]; }
     static constexpr int NT = 1 << (K - R);
     static constexpr int NS = 1 << R;
     static constexpr int NW = NT / 32;
@@ -297,7 +308,7 @@ struct Sweep {
         static_for<0, R>([&](auto bc) {
             constexpr int b = decltype(bc)::value;
             constexpr int tb = reg_bit<g, b>();
-            constexpr int rk = rank_of(K, KIND, tb);
+            constexpr int rk = rank_of(K, LK, tb);
             if constexpr (rk < rot_lo<g>() || rk >= rot_hi<g>()) return;  // not rotated in this layout
             if (KIND == 1 && tb < c) return;                             // carried bit
             Real part = 0;
@@ -391,6 +402,20 @@ struct Sweep {
         if (KIND == 0) {
 #pragma unroll
             for (int m = 0; m < NS; ++m) f(m, (uint64_t)e_slot<0>(m));
+        } else if (KIND == 2) {
+            // runs of 2^kRunBits: layout 0's registers are tile bits
+            // [K - 1 - R, K - 1); the cl of them inside the run stay in place,
+            // the others lie on run 1 (consecutive global bits from g0)
+            constexpr int lo = K - 1 - R, cl = kRunBits - lo;
+            static_assert(cl >= 0 && cl <= R, "layout-0 registers straddle the run boundary");
+            const uint64_t stride = 1ull << tm.g0;
+            uint64_t hi = 0;
+#pragma unroll
+            for (int h = 0; h < (NS >> cl); ++h) {
+#pragma unroll
+                for (int l = 0; l < (1 << cl); ++l) f((h << cl) | l, hi + ((uint64_t)l << lo));
+                hi += stride;
+            }
         } else {
             constexpr int lo = K - R;  // regs of layout 0 are tile bits [K - R, K)
             if (tm.c + tm.n1 <= lo) {
@@ -419,7 +444,7 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
     using C2 = typename S::C2;
     constexpr int NS = S::NS, NW = S::NW, NSLOT = S::NSLOT;
     constexpr bool kGen = V == V_FULL, kPhase = V != V_LEAN, kRead = V == V_FULL;
-    static_assert(KIND == 0 || make_layout(K, R, KIND).regs[0][0] == K - R, "layout 0 holds the top R tile bits");
+    static_assert(KIND != 1 || make_layout(K, R, KIND).regs[0][0] == K - R, "layout 0 holds the top R tile bits");
     extern __shared__ __align__(128) unsigned char smraw[];
     C2* buf = reinterpret_cast<C2*>(smraw);                                      // [NA][2^K]
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + S::BUF_BYTES);
@@ -436,12 +461,11 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         }
         return lo;
     };
-    // Thread 0: TMA loads of global tile gt into the tile buffer.
     bool pending = false;
-    // Called by every thread.  Contiguous tiles: thread 0 issues one TMA bulk
-    // copy per array.  Strided tiles: every thread issues 16-byte cp.async
-    // copies (each request exactly one 32-byte sector of a row), completing on
-    // the same barrier.
+    // Called by every thread; every thread arrives once on the barrier.
+    // Contiguous tiles: thread 0 issues one TMA bulk copy per array.  Strided
+    // and run-structured tiles: every thread issues 16-byte cp.async copies,
+    // completing on the same barrier.
     auto issue = [&](int64_t gt) {
         const int ti = find_task(gt);
         const SweepTask& T = tasks[ti];
@@ -467,18 +491,37 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
             pending = true;
             return;
         }
-        if (tid != 0) return;
-        mbar_expect_tx(full, (uint32_t)S::BUF_BYTES);
+        // kind 0 / 2: thread 0 arrives with the byte count, every other thread
+        // arrives plainly.  Kind 0 (contiguous): one bulk copy per array by
+        // thread 0.  Kind 2 (runs of 2^c): one bulk copy per run and array by
+        // warp 0, after thread 0's byte count.
+        if (tid == 0) mbar_expect_tx(full, (uint32_t)S::BUF_BYTES);
+        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(full)) : "memory");
+        if (KIND == 0) {
+            if (tid == 0) {
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const C2* src = reinterpret_cast<const C2*>(a == 0 ? T.psi : T.lam) + ((uint64_t)tile << K);
-            tma_load_1d(buf + ((size_t)a << K), src, (uint32_t)S::TILE_BYTES, full);
+                for (int a = 0; a < NA; ++a) {
+                    const C2* src = reinterpret_cast<const C2*>(a == 0 ? T.psi : T.lam) + ((uint64_t)tile << K);
+                    tma_load_1d(buf + ((size_t)a << K), src, (uint32_t)S::TILE_BYTES, full);
+                }
+            }
+        } else if (tid < 32) {
+            __syncwarp();
+            const TMap tm{T.c, T.g0, T.n1, T.g1, K};
+            const uint64_t base = tm.base(tile);
+            constexpr uint32_t run = 1u << kRunBits;  // amplitudes per run (>= 16 bytes, aligned)
+            for (uint32_t e0 = tid * run; e0 < (1u << K); e0 += 32 * run)
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const C2* src = reinterpret_cast<const C2*>(a == 0 ? T.psi : T.lam) + base + tm.gofs(e0);
+                    tma_load_1d(buf + ((size_t)a << K) + e0, src, run * (uint32_t)sizeof(C2), full);
+                }
         }
         pending = true;
     };
 
     if (tid == 0) {
-        mbar_init(full, KIND == 1 ? S::NT : 1);
+        mbar_init(full, S::NT);  // one arrival per thread (with its copies, or with the byte count)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -518,7 +561,7 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         auto release = [&]() {
             __syncthreads();
             if (nx < total) {
-                if (tid == 0 && KIND == 0) fence_proxy_async();
+                if ((KIND == 0 && tid == 0) || (KIND == 2 && tid < 32)) fence_proxy_async();  // bulk-copy issuers
                 issue(nx);
             }
         };
@@ -536,12 +579,12 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
             if (ntr == 0 && nx < total) issue(nx);
         } else {
             const int ok = mbar_wait_bounded(full, parity) ? 1 : 0;
-            parity ^= 1u;
-            if (tid == 0) pending = false;
-            if (!__syncthreads_and(ok)) {
+            if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
                 if (tid == 0) atomicExch(err, 1);
                 break;
             }
+            parity ^= 1u;
+            if (tid == 0) pending = false;
 #pragma unroll
             for (int a = 0; a < NA; ++a) S::template lds_dense<0>(buf + ((size_t)a << K), v[a], tid);
             if (ntr == 0) release();

@@ -14,6 +14,7 @@ int sweep_c64f(int kind, int variant, bool grid_only, const SweepLaunch* L, int 
                cudaError_t* status) {
     QS_C64F(0, V_FULL) QS_C64F(0, V_PHASE) QS_C64F(0, V_LEAN)
     QS_C64F(1, V_FULL) QS_C64F(1, V_PHASE) QS_C64F(1, V_LEAN)
+    QS_C64F(2, V_FULL) QS_C64F(2, V_PHASE) QS_C64F(2, V_LEAN)
     if (status) *status = cudaErrorInvalidValue;
     return 0;
 }

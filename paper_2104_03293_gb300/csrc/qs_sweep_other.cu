@@ -14,6 +14,7 @@ int sweep_other(int dtype, int adjoint, int kind, bool grid_only, const SweepLau
                 cudaError_t* status) {
     QS_OTH(0, 1, float, 13, 5, 2, 0)
     QS_OTH(0, 1, float, 13, 5, 2, 1)
+    QS_OTH(0, 1, float, 13, 5, 2, 2)
     QS_OTH(1, 0, double, 12, 5, 1, 0)
     QS_OTH(1, 0, double, 12, 5, 1, 1)
     QS_OTH(1, 1, double, 12, 4, 2, 0)

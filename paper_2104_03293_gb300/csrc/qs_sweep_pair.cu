@@ -1,0 +1,385 @@
+// Packed-pair sweep: the strided complex64 forward sweeps (rotations only, or
+// rotations with a layer boundary and its phase), layouts in qs_pair.h.
+//
+// Same tile walk as sweep_kernel (qs_sweep.cuh): persistent CTAs, two per SM,
+// one in-place 64 KB tile buffer, 16-byte cp.async copies of the strided tile
+// completing on an mbarrier (bounded wait), the next tile's copies issued
+// after the current tile's last shared-memory read.  The difference is the
+// register format: pairs split by component and updated with packed f32x2
+// FMAs (fma.rn.f32x2), transposes as 16-byte pair moves.
+#include "qs_pair.h"
+#include "qs_sweep.cuh"
+
+namespace qs {
+
+namespace {
+
+// a * b + c on both halves: one packed f32x2 FMA (fma.rn.f32x2)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One 8-byte store of an amplitude whose parts sit in different pairs.  Two
+// 4-byte stores would leave each 32-byte sector half written in between,
+// which costs DRAM reads; the vector store writes whole sectors.
+__device__ __forceinline__ void stg2(float2* p, float re, float im) {
+    asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(re), "f"(im) : "memory");
+}
+
+template <int C>
+struct PairSweep {
+    static constexpr int K = kPairK, NT = 128, NJ = 32, P = C;
+    static constexpr int NB = 1;  // tile buffers per CTA
+    static constexpr size_t BUF_BYTES = (size_t)8 << K;
+    static constexpr size_t SMEM_BYTES = NB * BUF_BYTES + 64;
+
+    template <int g, int t> __host__ __device__ static constexpr int tb() { return pair_layout(C).tbits[g][t]; }
+    template <int g, int b> __host__ __device__ static constexpr int rb() { return pair_layout(C).regs[g][b]; }
+    template <int g> __host__ __device__ static constexpr int rmask() { return pair_layout(C).rotmask[g]; }
+
+    template <int g>
+    __device__ static __forceinline__ uint32_t e_thread(uint32_t tid) {
+        uint32_t e = 0;
+        static_for<0, 7>([&](auto tc) {
+            constexpr int t = decltype(tc)::value;
+            e |= ((tid >> t) & 1u) << tb<g, t>();
+        });
+        return e;
+    }
+    template <int g>
+    __host__ __device__ static constexpr uint32_t e_slot(int j) {
+        uint32_t e = 0;
+        for (int b = 0; b < 5; ++b) e |= (uint32_t)((j >> b) & 1) << pair_layout(C).regs[g][b];
+        return e;
+    }
+
+    // ---- transposes (16-byte pair units, swizzled) ---------------------------
+    template <int g>
+    __device__ static __forceinline__ void sts(float4* tb4, const float2 (&X)[NJ], const float2 (&Y)[NJ],
+                                               uint32_t tid) {
+        const uint32_t pt = pair_phys(pair_unit(e_thread<g>(tid), P));
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+            tb4[pt ^ pair_phys(pair_unit(e_slot<g>(j), P))] = make_float4(X[j].x, X[j].y, Y[j].x, Y[j].y);
+    }
+    template <int g>
+    __device__ static __forceinline__ void lds(const float4* tb4, float2 (&X)[NJ], float2 (&Y)[NJ], uint32_t tid) {
+        const uint32_t pt = pair_phys(pair_unit(e_thread<g>(tid), P));
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const float4 v = tb4[pt ^ pair_phys(pair_unit(e_slot<g>(j), P))];
+            X[j] = make_float2(v.x, v.y);
+            Y[j] = make_float2(v.z, v.w);
+        }
+    }
+    // from the landing buffer (tile order, one float2 per amplitude) into layout 0
+    __device__ static __forceinline__ void lds_dense(const float2* src, float2 (&X)[NJ], float2 (&Y)[NJ],
+                                                     uint32_t tid) {
+        const uint32_t et = e_thread<0>(tid);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const float2 a = src[et | e_slot<0>(j)];
+            const float2 b = src[et | e_slot<0>(j) | (1u << P)];
+            X[j] = make_float2(a.x, b.x);
+            Y[j] = make_float2(a.y, b.y);
+        }
+    }
+
+    // ---- rotations: a' = a + w (-i b), b' = b + w (-i a) ----------------------
+    template <int g>
+    __device__ static __forceinline__ void rotate(float2 (&X)[NJ], float2 (&Y)[NJ], float w) {
+        const float2 w2 = make_float2(w, w), nw2 = make_float2(-w, -w);
+        static_for<0, 5>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            if constexpr (((rmask<g>() >> b) & 1) != 0) {
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    if (j & (1 << b)) continue;
+                    const int j2 = j | (1 << b);
+                    const float2 xa = X[j], ya = Y[j], xb = X[j2], yb = Y[j2];
+                    X[j] = ffma2(w2, yb, xa);
+                    Y[j] = ffma2(nw2, xb, ya);
+                    X[j2] = ffma2(w2, ya, xb);
+                    Y[j2] = ffma2(nw2, xa, yb);
+                }
+            }
+        });
+        if (g == 0) {  // the pack bit: the two halves of every pair
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                const float ar = X[j].x, br = X[j].y, ai = Y[j].x, bi = Y[j].y;
+                X[j] = make_float2(fmaf(w, bi, ar), fmaf(w, ai, br));
+                Y[j] = make_float2(fmaf(-w, br, ai), fmaf(-w, ar, bi));
+            }
+        }
+    }
+
+    // ---- phase: slot m = lane | j << 1 (cost program of the layout) ------------
+    template <int g>
+    __device__ static __forceinline__ void phase(float2 (&X)[NJ], float2 (&Y)[NJ], const SweepTask& T,
+                                                 uint64_t zthread, const float2* __restrict__ tab, int frame) {
+        const uint64_t fm = frame ? ((1ull << T.n) - 1ull) : 0ull;
+        SlotCost<6> sc;
+        sc.init(T.cprog[g], zthread ^ fm, frame, T.cost_lo);
+        const int top = T.tab_stride - 1;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const float2 fa = __ldg(tab + sc.tidx(2 * j, top));
+            const float2 fb = __ldg(tab + sc.tidx(2 * j + 1, top));
+            const float ar = X[j].x, br = X[j].y, ai = Y[j].x, bi = Y[j].y;
+            X[j] = make_float2(fmaf(ar, fa.x, -ai * fa.y), fmaf(br, fb.x, -bi * fb.y));
+            Y[j] = make_float2(fmaf(ar, fa.y, ai * fa.x), fmaf(br, fb.y, bi * fb.x));
+        }
+    }
+};
+
+}  // namespace
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Two CTAs per SM, each with NB = 1 in-place tile buffer: after tile k's last
+// shared-memory read the buffer takes tile k + 1 (NB > 1 would keep more
+// tiles in flight per CTA, at one CTA per SM; measured slower).
+//
+// CL = 4: clusters of four CTAs take the four tiles that differ in tile-index
+// bits 0 and 1 (the neighbouring runs of one 128-byte line when c = 2) and
+// issue their copies together, after a cluster barrier, so the HBM lines they
+// share are fetched once.  Every CTA of a cluster walks the same number of
+// tiles (the tile count and the grid are multiples of four) and passes the
+// barrier once per tile, also after a timed-out wait.
+template <int C, int V, int CL>
+__global__ void __launch_bounds__(128, 2)
+    sweep_pair_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
+                      int64_t total, int* __restrict__ err) {
+    using S = PairSweep<C>;
+    constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NB = S::NB;
+    constexpr bool kPhase = V != V_LEAN;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
+    const uint32_t tid = threadIdx.x;
+    float2 X[NJ], Y[NJ];
+
+    auto find_task = [&](int64_t gt) -> int {
+        if (ntasks == 1) return 0;
+        int lo = 0, hi = ntasks - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(prefix + mid) <= gt) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    };
+    uint32_t pend = 0;   // buffers with copies in flight
+    uint32_t phase = 0;  // per buffer: parity of its next completion
+    // every thread: 16-byte cp.async copies of its share of the strided tile
+    // gt into buffer b, completing on that buffer's barrier (one arrival per
+    // thread)
+    auto issue = [&](int64_t gt, int b) {
+        const int ti = find_task(gt);
+        const SweepTask& T = tasks[ti];
+        const int64_t tile = gt - __ldg(prefix + ti);
+        const TMap tm{T.c, T.g0, T.n1, T.g1, K};
+        const float2* src = reinterpret_cast<const float2*>(T.psi) + tm.base(tile);
+        float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
+        for (int q = tid; q < (1 << K) / 2; q += NT) {
+            const uint32_t e = (uint32_t)q * 2;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + e)), "l"(src + tm.gofs(e))
+                         : "memory");
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full + b)) : "memory");
+        pend |= 1u << b;
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) mbar_init(full + b, NT);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    for (int b = 0; b < NB; ++b) {
+        const int64_t g0 = (int64_t)blockIdx.x + (int64_t)b * gridDim.x;
+        if (g0 < total) issue(g0, b);
+    }
+
+    bool failed = false;
+    int b = 0;  // buffer of the current tile
+    for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x, b = (b + 1 == NB ? 0 : b + 1)) {
+        const int ti = find_task(gt);
+        const SweepTask& T = tasks[ti];
+        const int64_t tile = gt - __ldg(prefix + ti);
+        const int flags = T.flags, nr = T.nrounds;
+        const TMap tm{T.c, T.g0, T.n1, T.g1, K};
+        const uint64_t base = tm.base(tile);
+        const int64_t nx = gt + (int64_t)NB * gridDim.x;
+        float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
+        float4* buf4 = reinterpret_cast<float4*>(buf);
+        // transposes of this tile: one per round, plus one back to layout 0
+        const int ntr = nr + (nr & 1);
+        int done_tr = 0;
+        auto release = [&]() {
+            if (CL > 1) cluster_sync_all();
+            else __syncthreads();
+            if (nx < total && !failed) issue(nx, b);
+        };
+
+        if (failed) {  // a copy timed out earlier: keep the cluster barriers in step
+            release();
+            continue;
+        }
+        const int ok = mbar_wait_bounded(full + b, (phase >> b) & 1u) ? 1 : 0;
+        if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
+            if (tid == 0) atomicExch(err, 1);
+            failed = true;
+            if (CL == 1) break;
+            release();
+            continue;
+        }
+        phase ^= 1u << b;
+        pend &= ~(1u << b);
+        S::lds_dense(buf, X, Y, tid);
+        __syncthreads();  // dense reads done before the swizzled writes
+
+        int cur = 0;
+        auto to_layout = [&](int g) {
+            if (g == cur) return;
+            if (cur == 0) S::template sts<0>(buf4, X, Y, tid);
+            else S::template sts<1>(buf4, X, Y, tid);
+            __syncthreads();
+            if (g == 0) S::template lds<0>(buf4, X, Y, tid);
+            else S::template lds<1>(buf4, X, Y, tid);
+            cur = g;
+            if (++done_tr == ntr) release();
+        };
+        auto do_phase = [&](const float2* ltab, int frame) {
+            if (cur == 0)
+                S::template phase<0>(X, Y, T, base + tm.gofs(S::template e_thread<0>(tid)), ltab, frame);
+            else
+                S::template phase<1>(X, Y, T, base + tm.gofs(S::template e_thread<1>(tid)), ltab, frame);
+        };
+        const float2* tab = reinterpret_cast<const float2*>(T.tab);
+        for (int r = 0; r < nr; ++r) {
+            const SweepRound rd = T.rounds[r];
+            const LayerDev ly = T.layers[rd.layer];
+            const float2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
+            if (kPhase && rd.phase_pre) do_phase(ltab, ly.frame);
+            const float w = (float)ly.w;
+            // zig-zag: a round starts in the current layout
+            if (cur == 0) {
+                S::template rotate<0>(X, Y, w);
+                to_layout(1);
+                S::template rotate<1>(X, Y, w);
+            } else {
+                S::template rotate<1>(X, Y, w);
+                to_layout(0);
+                S::template rotate<0>(X, Y, w);
+            }
+            if (kPhase && rd.phase_post) do_phase(ltab, ly.frame);
+        }
+        to_layout(0);
+
+        if (flags & T_STORE) {
+            float2* dst = reinterpret_cast<float2*>(T.psi) + base + tm.gofs(S::template e_thread<0>(tid));
+            const uint64_t gP = tm.gofs(1u << P);
+            if (T.c + T.n1 <= 8) {  // layout-0 registers (tile bits 8..12) in the second run: one shift
+                const int sh = T.g1 + 8 - T.c - T.n1;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    float2* d = dst + ((uint64_t)j << sh);
+                    stg2(d, X[j].x, Y[j].x);
+                    stg2(d + gP, X[j].y, Y[j].y);
+                }
+            } else {  // the map is additive over disjoint bits: Gray-code walk over j
+                uint64_t step[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) step[q] = tm.gofs(1u << (8 + q));
+                uint64_t off = 0;
+#pragma unroll
+                for (int i = 0; i < NJ; ++i) {
+                    const int j = i ^ (i >> 1);
+                    if (i > 0) {
+                        const int q = __ffs(i) - 1;
+                        if ((j >> q) & 1) off += step[q];
+                        else off -= step[q];
+                    }
+                    stg2(dst + off, X[j].x, Y[j].x);
+                    stg2(dst + off + gP, X[j].y, Y[j].y);
+                }
+            }
+        }
+    }
+    // before the shared memory goes away: wait (bounded) for copies in flight
+    if (tid == 0)
+        for (int q = 0; q < NB; ++q)
+            if ((pend >> q) & 1u) mbar_wait_bounded(full + q, (phase >> q) & 1u);
+    __syncthreads();
+}
+
+template <int C, int V>
+static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)PairSweep<C>::SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)PairSweep<C>::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (L.total_tiles % 4 == 0 && grid % 4 == 0 && grid >= 4) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(PairSweep<C>::NT);
+        cfg.dynamicSmemBytes = PairSweep<C>::SMEM_BYTES;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 4;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, sweep_pair_kernel<C, V, 4>, L.tasks, L.tile_prefix, L.ntasks,
+                                           L.total_tiles, L.err);
+        return note_launch(e);
+    }
+    sweep_pair_kernel<C, V, 1><<<grid, PairSweep<C>::NT, PairSweep<C>::SMEM_BYTES, st>>>(
+        L.tasks, L.tile_prefix, L.ntasks, L.total_tiles, L.err);
+    return note_launch(cudaGetLastError());
+}
+
+cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st) {
+    if (L.pairc == 2 && L.variant == V_LEAN) return launch_pair_cfg<2, V_LEAN>(L, grid, st);
+    if (L.pairc == 2 && L.variant == V_PHASE) return launch_pair_cfg<2, V_PHASE>(L, grid, st);
+    if (L.pairc == 3 && L.variant == V_LEAN) return launch_pair_cfg<3, V_LEAN>(L, grid, st);
+    if (L.pairc == 3 && L.variant == V_PHASE) return launch_pair_cfg<3, V_PHASE>(L, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+// Persistent grid: as many four-CTA clusters as can be resident at once
+// (a multiple of four), else one CTA per resident slot.
+int sweep_pair_grid() {
+    auto kern = sweep_pair_kernel<2, V_PHASE, 4>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PairSweep<2>::SMEM_BYTES);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(4);
+    cfg.blockDim = dim3(PairSweep<2>::NT);
+    cfg.dynamicSmemBytes = PairSweep<2>::SMEM_BYTES;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 4;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0) return 4 * ncl;
+    cudaGetLastError();
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V_PHASE, 1>, PairSweep<2>::NT,
+                                                  PairSweep<2>::SMEM_BYTES);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * sms;
+}
+
+}  // namespace qs

@@ -36,15 +36,23 @@ def make_layout(K, R, kind):
 PAGE_BIT = {"c64": 18, "c128": 17}
 
 
+FAR_BIT_C64 = 22
+
+
 def make_shapes(nphys, KA, KB, cmin, page_bit=18):
-    shapes = [dict(K=KA, c=0, g0=0, nt=KA - 1, kind=0, n1=0, g1=0)]
-    lo = KA - 1
+    a = dict(K=KA, c=0, g0=0, nt=KA - 1, kind=0, n1=0, g1=0)
+    lo, hi, split = KA - 1, nphys, page_bit
+    if KA == 13 and KB == 13 and nphys >= 30:
+        f = 4
+        a.update(c=KA - 1 - f, g0=nphys - f, n1=f, g1=KA - 1 - f)
+        lo, hi, split = a["c"], nphys - f, FAR_BIT_C64
+    shapes = [a]
     per = KB - cmin
-    rest = nphys - lo
+    rest = hi - lo
     if rest <= 0:
         return shapes
     S = -(-rest // per)
-    below = max(0, min(page_bit, nphys) - lo)
+    below = max(0, min(split, hi) - lo)
     high = rest - below
     nt = [min(per, rest - k * per) for k in range(S)]
     nh = [0] * S
@@ -66,30 +74,46 @@ def make_shapes(nphys, KA, KB, cmin, page_bit=18):
     return shapes
 
 
+def contiguous(sh):
+    return sh["kind"] == 0 and sh["c"] == 0 and sh["n1"] == 0
+
+
 def gofs(e, sh):
     c, g0, n1, g1 = sh["c"], sh["g0"], sh["n1"], sh["g1"]
     return (e & ((1 << c) - 1)) | (((e >> c) & ((1 << n1) - 1)) << g0) | ((e >> (c + n1)) << g1)
 
 
 def tile_base(t, sh):
+    """Non-tile global bits, ascending, take the bits of the tile index t."""
     K, c, g0, n1, g1 = sh["K"], sh["c"], sh["g0"], sh["n1"], sh["g1"]
-    if sh["kind"] == 0:
+    if contiguous(sh):
         return t << K
-    la, lb = g0 - c, g1 - (g0 + n1)
-    ma = (1 << la) - 1 if la > 0 else 0
-    mb = (1 << lb) - 1 if lb > 0 else 0
-    return ((t & ma) << c) | (((t >> la) & mb) << (g0 + n1)) | ((t >> (la + lb)) << (g1 + K - c - n1))
+    runs = sorted((g, l) for g, l in ((g0, n1), (g1, K - c - n1)) if l > 0)
+    out, pos, bit = 0, c, 0
+    for g, l in runs + [(200, 0)]:
+        for q in range(pos, g):
+            if (t >> bit) == 0:
+                return out
+            out |= ((t >> bit) & 1) << q
+            bit += 1
+        pos = g + l
+    return out
 
 
 def tile_to_global(e, sh):
-    return e if sh["kind"] == 0 else gofs(e, sh)
+    return e if contiguous(sh) else gofs(e, sh)
 
 
 def slot_off0(m, sh, R, lay0):
     """Global offset of register slot m in layout 0 (the kernel's for_slots)."""
     K = sh["K"]
     if sh["kind"] == 0:
-        return sum(((m >> b) & 1) << lay0["regs"][b] for b in range(R))
+        if contiguous(sh):
+            return sum(((m >> b) & 1) << lay0["regs"][b] for b in range(R))
+        lo = K - 1 - R  # registers: tile bits [lo, K - 1); below c in place, the rest on run 1
+        cl = sh["c"] - lo
+        assert cl >= 0 and sh["n1"] >= K - 1 - sh["c"]
+        return ((m & ((1 << cl) - 1)) << lo) | ((m >> cl) << sh["g0"])
     lo = K - R
     if sh["c"] + sh["n1"] <= lo:
         return m << (sh["g1"] + lo - sh["c"] - sh["n1"])
@@ -106,3 +130,24 @@ def e_slot(m, lay):
 
 def phys(e, R):
     return e ^ ((e >> R) & 31)
+
+
+# Packed-pair layouts (qs_pair.h): strided complex64 tiles with c = 2 or 3.
+PAIR_K = 13
+
+
+def pair_layout(C):
+    regs0 = [8, 9, 10, 11, 12]
+    if C == 2:
+        return dict(P=2, regs=[regs0, [3, 4, 5, 6, 7]], tbits=[[0, 1, 3, 4, 5, 6, 7], [0, 1, 9, 8, 10, 11, 12]],
+                    rotmask=[0x1f, 0x1f])
+    return dict(P=3, regs=[regs0, [4, 5, 6, 7, 12]], tbits=[[0, 1, 2, 4, 5, 6, 7], [0, 1, 2, 8, 9, 10, 11]],
+                rotmask=[0x1f, 0x0f])
+
+
+def pair_unit(e, P):
+    return (e & ((1 << P) - 1)) | ((e >> (P + 1)) << P)
+
+
+def pair_phys(u):
+    return u ^ ((u >> 3) & 7) ^ ((u >> 6) & 7) ^ ((u >> 9) & 7)

@@ -12,8 +12,8 @@ the GPU as an out-of-bounds access.
 import numpy as np
 import pytest
 
-from layout_mirror import (CFG, MIN_PHYS, PAGE_BIT, e_slot, e_thread, make_layout, make_shapes, phys, rank_of,
-                           slot_off0, tile_base, tile_to_global)
+from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_layout,
+                           pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
 
 
 @pytest.mark.parametrize("key", list(CFG))
@@ -32,10 +32,12 @@ def test_every_sweep_is_a_bijection(key):
             owned += [gbit(tb, sh) for tb in range(sh["K"] - 1 if sh["kind"] == 0 else sh["K"])
                       if sh["kind"] == 0 or tb >= sh["c"]]
         assert sorted(owned) == list(range(nphys))
-        if nphys >= 34 and key[0] == "c64":
-            # the page footprint of the strided tiles is balanced: 2^8 pages each
-            assert max(sum(1 for tb in range(sh["c"], sh["K"]) if gbit(tb, sh) >= page)
-                       for sh in shapes[1:]) == 8
+        if nphys >= 30 and key[0] == "c64":
+            # the largest states spread the far bits: shape A takes the top
+            # four qubits (2 KB runs), the strided shapes at most four each
+            assert shapes[0]["c"] == 8 and owned[8:12] == list(range(nphys - 4, nphys))
+            assert max(sum(1 for tb in range(sh["c"], sh["K"]) if gbit(tb, sh) >= FAR_BIT_C64)
+                       for sh in shapes[1:]) <= 4
         for sh in shapes:
             K, c, g0, nt = sh["K"], sh["c"], sh["g0"], sh["nt"]
             assert K - R >= 5 and K <= nphys
@@ -92,3 +94,37 @@ def test_swizzle_is_conflict_free(key):
                         for w in range(0, 32, group):
                             assert len({a % group for a in addrs[w:w + group]}) == group, (key, kind, li, m)
 
+
+
+@pytest.mark.parametrize("C", [2, 3])
+def test_pair_layouts(C):
+    """Packed-pair layouts: (thread, pair, half) covers the tile once in both
+    layouts; every target [C, 13) is rotated exactly once per round (the pack
+    bit in layout 0); the 16-byte transposes are conflict-free per
+    quarter-warp; the layout-0 store offsets reduce to one shift when the
+    first target run ends below tile bit 8."""
+    L = pair_layout(C)
+    P = L["P"]
+    for g in range(2):
+        regs, tb = L["regs"][g], L["tbits"][g]
+        assert sorted(regs + tb + [P]) == list(range(PAIR_K))
+        es = [sum(((j >> b) & 1) << regs[b] for b in range(5)) for j in range(32)]
+        et = [sum(((t >> i) & 1) << tb[i] for i in range(7)) for t in range(128)]
+        allv = {a | s | (h << P) for a in et for s in es for h in range(2)}
+        assert len(allv) == 1 << PAIR_K
+        for j in range(32):
+            for w0 in range(0, 128, 32):
+                for q in range(0, 32, 8):
+                    banks = {pair_phys(pair_unit(et[w0 + q + l] | es[j], P)) % 8 for l in range(8)}
+                    assert len(banks) == 8, (C, g, j, w0, q)
+    rotated = [P] + [L["regs"][g][b] for g in range(2) for b in range(5) if (L["rotmask"][g] >> b) & 1]
+    assert sorted(rotated) == list(range(C, PAIR_K))
+    assert len({pair_phys(u) for u in range(1 << (PAIR_K - 1))}) == 1 << (PAIR_K - 1)
+    for n in (24, 25, 28, 30, 32, 33, 34):
+        for sh in make_shapes(n, 13, 13, 2, PAGE_BIT["c64"])[1:]:
+            if sh["c"] != C:
+                continue
+            assert sh["K"] == PAIR_K
+            if sh["c"] + sh["n1"] <= 8:
+                shift = sh["g1"] + 8 - sh["c"] - sh["n1"]
+                assert all(tile_to_global(j << 8, sh) == j << shift for j in range(32))
