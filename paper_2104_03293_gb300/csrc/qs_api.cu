@@ -199,7 +199,7 @@ struct qs_state {
     Uploader up, up_ang;
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
-    int grid[2][4] = {};  // [adjoint][kernel kind; 3 = packed-pair kernel]
+    int grid[2][5] = {};  // [adjoint][kernel kind; 3, 4 = packed-pair kernel, phase / lean]
     int device = 0;
 };
 
@@ -302,7 +302,7 @@ int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* 
 // Grid size of the persistent sweep kernel for a tile shape.
 static int grid_for(qs_handle h, int kind, int adjoint) {
     int& g = h->grid[adjoint][kind];
-    if (!g) g = kind == 3 ? sweep_pair_grid() : sweep_grid(h->dtype, adjoint, kind);
+    if (!g) g = kind >= 3 ? sweep_pair_grid(kind == 4 ? 2 : 1) : sweep_grid(h->dtype, adjoint, kind);
     return g;
 }
 
@@ -442,7 +442,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
                       reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
-        e = launch_sweep(L, L.pairc ? grid_for(h, 3, 0) : grid_for(h, L.kind, 0), h->st);
+        e = launch_sweep(L, L.pairc ? grid_for(h, L.variant == 2 ? 4 : 3, 0) : grid_for(h, L.kind, 0), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
     }
     e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + rd_off), 1, h->st);

@@ -147,8 +147,11 @@ __device__ __forceinline__ void cluster_sync_all() {
 // share are fetched once.  Every CTA of a cluster walks the same number of
 // tiles (the tile count and the grid are multiples of four) and passes the
 // barrier once per tile, also after a timed-out wait.
+// Rotation-only sweeps hold fewer live values and fit three CTAs per SM.
+template <int V> struct PairOcc { static constexpr int value = 3; };
+
 template <int C, int V, int CL>
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(128, PairOcc<V>::value)
     sweep_pair_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
                       int64_t total, int* __restrict__ err) {
     using S = PairSweep<C>;
@@ -356,8 +359,9 @@ cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st) {
 
 // Persistent grid: as many four-CTA clusters as can be resident at once
 // (a multiple of four), else one CTA per resident slot.
-int sweep_pair_grid() {
-    auto kern = sweep_pair_kernel<2, V_PHASE, 4>;
+template <int V>
+static int pair_grid_v() {
+    auto kern = sweep_pair_kernel<2, V, 4>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PairSweep<2>::SMEM_BYTES);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(4);
@@ -376,10 +380,12 @@ int sweep_pair_grid() {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V_PHASE, 1>, PairSweep<2>::NT,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V, 1>, PairSweep<2>::NT,
                                                   PairSweep<2>::SMEM_BYTES);
     if (per_sm < 1) per_sm = 1;
     return per_sm * sms;
 }
+
+int sweep_pair_grid(int variant) { return variant == V_LEAN ? pair_grid_v<V_LEAN>() : pair_grid_v<V_PHASE>(); }
 
 }  // namespace qs
