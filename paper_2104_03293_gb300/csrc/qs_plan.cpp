@@ -165,6 +165,9 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit) {
         lo = a.c;
         hi = nphys - f;
         split = kFarBitC64;
+        // the sweep kernel relies on this structure (tile index = bits
+        // [kRunBits + 1, nphys - f), i.e. base = tile << (kRunBits + 1))
+        if (a.g0 + a.n1 != nphys || a.g1 != kRunBits || a.c + a.n1 + 1 != cfg.K_A) return {};
     }
     v.push_back(a);
     const int per = cfg.K_B - cfg.c_min;                   // targets per strided shape

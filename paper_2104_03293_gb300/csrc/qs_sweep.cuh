@@ -508,7 +508,9 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         } else if (tid < 32) {
             __syncwarp();
             const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-            const uint64_t base = tm.base(tile);
+            // runs of 2^kRunBits with the batch bit above them and run 1 on the
+            // top global bits: the tile index fills the bits in between
+            const uint64_t base = (uint64_t)tile << (kRunBits + 1);
             constexpr uint32_t run = 1u << kRunBits;  // amplitudes per run (>= 16 bytes, aligned)
             for (uint32_t e0 = tid * run; e0 < (1u << K); e0 += 32 * run)
 #pragma unroll
@@ -542,7 +544,9 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         const int64_t tile = gt - __ldg(prefix + ti);
         const int c = T.c, flags = T.flags, nr = T.nrounds;
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-        const uint64_t base = KIND == 0 ? ((uint64_t)tile << K) : tm.base(tile);
+        const uint64_t base = KIND == 0   ? ((uint64_t)tile << K)
+                              : KIND == 2 ? ((uint64_t)tile << (kRunBits + 1))
+                                          : tm.base(tile);
         // layouts that hold targets (kind 1 drops those entirely below c)
         int ga = S::G;
         if (KIND == 1) {

@@ -36,6 +36,8 @@ def test_every_sweep_is_a_bijection(key):
             # the largest states spread the far bits: shape A takes the top
             # four qubits (2 KB runs), the strided shapes at most four each
             assert shapes[0]["c"] == 8 and owned[8:12] == list(range(nphys - 4, nphys))
+            # the kernel takes the run-structured tile base as tile << 9
+            assert all(tile_base(t, shapes[0]) == t << 9 for t in (1, 2, 3, 5, (1 << (nphys - 13)) - 1))
             assert max(sum(1 for tb in range(sh["c"], sh["K"]) if gbit(tb, sh) >= FAR_BIT_C64)
                        for sh in shapes[1:]) <= 4
         for sh in shapes:
