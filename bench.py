@@ -151,6 +151,94 @@ def aggregate_value(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
+def secondary_workloads(qs, I, torch):
+    """The other targets, timed with CUDA events after the main run:
+    batched forwards of 512 uneven instances against the same instances one
+    at a time (tiled and plain per-gate launches); the n=26 p=10 gradient
+    against a forward and against 4p plain forwards (central differences);
+    64 instances x 200 Adam steps replayed from a CUDA graph."""
+    import numpy as np
+    out = {}
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # batched forwards: 512 instances, n ~ U{16..24}, p ~ U{1..10}
+    items = I.config2()
+    insts = [it[0] for it in items]
+    gs, bs = [it[1] for it in items], [it[2] for it in items]
+    bt = qs.Batch([x.n for x in insts])
+    for i, x in enumerate(insts):
+        bt.set_ising(i, x.h, x.edges, x.J)
+
+    def run_batch():
+        bt.evolve(gs, bs)
+        bt.results()
+    t_batch = timed(run_batch, 3)
+    states = []
+    for x in insts:
+        st = qs.State(x.n)
+        st.set_ising(x.h, x.edges, x.J)
+        states.append(st)
+
+    def run_seq(path):
+        for st, g, b in zip(states, gs, bs):
+            st.set_path(path)
+            st.evolve(g, b)
+            st.readout()
+    t_seq = timed(lambda: run_seq(qs.QS_PATH_TILED))
+    t_plain = timed(lambda: run_seq(qs.QS_PATH_PLAIN))
+    for st in states:
+        st.close()
+    bt.close()
+    upd = float(sum((x.n + 1) * (2 ** x.n) * len(g) for x, g in zip(insts, gs)))
+    out["batched_512"] = {"ms": t_batch, "one_at_a_time_tiled_ms": t_seq, "one_at_a_time_plain_ms": t_plain,
+                          "speedup_vs_tiled": t_seq / t_batch, "speedup_vs_plain": t_plain / t_batch,
+                          "amplitude_updates_per_s": upd / (t_batch / 1e3)}
+    # gradient at n=26, p=10 (MaxCut) against forwards
+    inst, g, b = I.config3()
+    st = qs.State(inst.n)
+    st.set_ising(inst.h, inst.edges, inst.J)
+
+    def fwd():
+        st.evolve(g, b)
+        st.readout()
+    t_fwd = timed(fwd, 3)
+    t_grad = timed(lambda: st.grad(g, b, qs.QS_OBJ_ENERGY), 3)
+    st.set_path(qs.QS_PATH_PLAIN)
+    t_plain_fwd = timed(fwd, 2)
+    st.close()
+    out["grad_n26_p10"] = {"grad_ms": t_grad, "forward_ms": t_fwd, "forward_equivalents": t_grad / t_fwd,
+                           "fd_ms": 4 * len(g) * t_plain_fwd, "speedup_vs_fd": 4 * len(g) * t_plain_fwd / t_grad}
+    # 64 instances x 200 Adam steps in a CUDA graph
+    items = I.config4()
+    insts = [it[0] for it in items]
+    bt = qs.Batch([x.n for x in insts])
+    g0, b0 = [], []
+    for i, (x, pk, tau) in enumerate(items):
+        bt.set_ising(i, x.h, x.edges, x.J)
+        gg, bb = qs.aqa_angles(tau, np.arange(1, pk + 1) / (pk + 1))
+        g0.append(gg)
+        b0.append(bb)
+    bt.evolve(g0, b0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt.adam(g0, b0, 200, use_graph=True)
+    E, P = bt.results()
+    t_adam = 1e3 * (time.perf_counter() - t0)
+    bt.close()
+    out["adam_64x200"] = {"ms": t_adam, "mean_E": float(np.mean(E)), "mean_P_ground": float(np.mean(P))}
+    return out
+
+
 def workload_config(args):
     return {"workload": f"AQA n={args.n} p={args.p} tau={args.tau} forward + readout (ER(4) Ising, h,J in "
                         f"U{{-1,0,1}}); grad of P_ground at n={args.grad_n} wrt tau and {args.p} knots",
@@ -196,6 +284,7 @@ def main():
     ap.add_argument("--grad-n", type=int, default=33)
     ap.add_argument("--ref-n", type=int, default=26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the batched / n=26 gradient / Adam figures")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -296,6 +385,7 @@ def main():
     e2e_s = statistics.mean(timing["e2e_s"])
     h2d = inst.h.nbytes + inst.edges.nbytes + inst.J.nbytes + 2 * 8 * p
     d2h = 3 * 8
+    extra = None if args.no_secondary else secondary_workloads(qs, I, torch)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v_cpu, dt_cpu, thr, L = oracle_sample(args.ref_n, target_s=12.0)
@@ -322,6 +412,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "readout": {"E": E, "P_ground": P, "grad_P": v, "dP_dtau": dtau},
+        "secondary": extra,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -139,6 +139,17 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
             prog_pair[s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, 6));
         }
     }
+    for (size_t s = 0; s < shapes[1].size(); ++s) {
+        const Shape& sh = shapes[1][s];
+        if (!pair_choice(dtype, 1, sh.kind, sh.c, 0)) continue;
+        const PairAdjLayout PL = pair_adj_layout(sh.c);
+        for (int g = 0; g < 3; ++g) {
+            int regq[6] = {-1, -1, -1, -1, -1, -1};
+            regq[0] = shape_bit(sh, PL.P);  // slot bit 0: the pack bit; bits 1..4: regs[g]
+            for (int b = 0; b < 4; ++b) regq[1 + b] = shape_bit(sh, PL.regs[g][b]);
+            prog_pair_adj[s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, 5));
+        }
+    }
     {
         int regq[6];
         for (int b = 0; b < 6; ++b) regq[b] = b < n ? b : -1;
@@ -302,7 +313,9 @@ int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* 
 // Grid size of the persistent sweep kernel for a tile shape.
 static int grid_for(qs_handle h, int kind, int adjoint) {
     int& g = h->grid[adjoint][kind];
-    if (!g) g = kind >= 3 ? sweep_pair_grid(kind == 4 ? 2 : 1) : sweep_grid(h->dtype, adjoint, kind);
+    if (!g)
+        g = kind < 3 ? sweep_grid(h->dtype, adjoint, kind)
+                     : (adjoint ? sweep_pair_adj_grid() : sweep_pair_grid(kind == 4 ? 2 : 1));
     return g;
 }
 
@@ -412,6 +425,8 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     }
     for (auto& s : rev) {
         SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective);
+        if (pair_choice(h->dtype, 1, sha[s.shape].kind, sha[s.shape].c, 0))
+            for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_pair_adj[s.shape][g]);
         rev_off.push_back(blob.add(&t, sizeof t));
         const int64_t pre[2] = {0, sha[s.shape].ntiles};
         rev_pre.push_back(blob.add(pre, sizeof pre));
@@ -451,7 +466,8 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         const Shape& sh = sha[rev[i].shape];
         SweepLaunch L{kernel_kind(sh), 0, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + rev_pre[i]), derr};
-        e = launch_sweep(L, grid_for(h, L.kind, 1), h->st);
+        L.pairc = pair_choice(h->dtype, 1, sh.kind, sh.c, 0);
+        e = launch_sweep(L, grid_for(h, L.pairc ? 3 : L.kind, 1), h->st);
         if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
         if (red_cnt[i]) {
             e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + red_off[i]), red_cnt[i], h->st);

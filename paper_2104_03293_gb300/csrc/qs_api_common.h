@@ -58,6 +58,7 @@ struct Instance {
     std::vector<Shape> shapes[2];                      // [forward, adjoint]
     size_t prog_off[2][kMaxShapes][kMaxLayouts] = {};  // int32 offsets into progs
     size_t prog_pair[kMaxShapes][2] = {};              // packed-pair layouts (forward shapes)
+    size_t prog_pair_adj[kMaxShapes][3] = {};          // packed-pair adjoint layouts (adjoint shapes)
     size_t enum_off = 0, plain_off = 0;
     int plain_nf = 0, plain_ne = 0, plain_const0 = 0;
     DevBuf progs;

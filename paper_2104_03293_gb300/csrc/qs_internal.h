@@ -111,9 +111,12 @@ std::vector<int32_t> build_cost_prog(int n, const std::vector<int32_t>& h, const
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All return cudaError_t.
 cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st);
+cudaError_t launch_sweep_pair_adj(const SweepLaunch& L, int grid, cudaStream_t st);
+int sweep_pair_adj_grid();
 int sweep_pair_grid(int variant);  // variant as sweep_variant: 1 phase, 2 rotations only
 // Packed-pair kernel choice for a sweep: the carried-bit count c when the
-// strided complex64 forward sweep without readout can use it, else 0.
+// strided complex64 sweep can use it (forward: without readout; adjoint:
+// every reverse sweep), else 0.
 int pair_choice(int dtype, int adjoint, int kind, int c, int variant);
 // ---------------------------------------------------------------------------
 // Launch accounting (qs_launch_count): every launcher reports its kernels.

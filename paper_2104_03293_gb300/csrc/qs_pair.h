@@ -72,6 +72,41 @@ QS_PHD constexpr PairLayout pair_layout(int C) {
     return t;
 }
 
+// Adjoint layouts (two arrays, 32 amplitudes = 16 pairs per array and
+// thread, 256 threads): the pack bit plus four register bits per layout and
+// three layouts.  Layout 0 holds the four top tile bits (coalesced stores).
+struct PairAdjLayout {
+    int C, P;
+    int regs[3][4];   // tile bit of pair-index bit b (ascending)
+    int tbits[3][8];  // tile bit of thread-index bit t (lane order)
+    int rotmask[3];   // bit b: regs[g][b] is rotated in layout g
+};
+
+QS_PHD constexpr PairAdjLayout pair_adj_layout(int C) {
+    PairAdjLayout t{};
+    t.C = C;
+    t.P = C;
+    const int r0[4] = {9, 10, 11, 12};
+    const int r1c2[4] = {3, 4, 5, 6}, r2c2[4] = {7, 8, 11, 12};
+    const int t0c2[8] = {0, 1, 3, 4, 5, 6, 7, 8}, t1c2[8] = {0, 1, 9, 7, 8, 10, 11, 12}, t2c2[8] = {0, 1, 3, 4, 5, 6, 9, 10};
+    const int r1c3[4] = {4, 5, 6, 7}, r2c3[4] = {8, 10, 11, 12};
+    const int t0c3[8] = {0, 1, 2, 4, 5, 6, 7, 8}, t1c3[8] = {0, 1, 2, 8, 9, 10, 11, 12}, t2c3[8] = {0, 1, 2, 4, 5, 6, 7, 9};
+    for (int b = 0; b < 4; ++b) {
+        t.regs[0][b] = r0[b];
+        t.regs[1][b] = C == 2 ? r1c2[b] : r1c3[b];
+        t.regs[2][b] = C == 2 ? r2c2[b] : r2c3[b];
+    }
+    for (int i = 0; i < 8; ++i) {
+        t.tbits[0][i] = C == 2 ? t0c2[i] : t0c3[i];
+        t.tbits[1][i] = C == 2 ? t1c2[i] : t1c3[i];
+        t.tbits[2][i] = C == 2 ? t2c2[i] : t2c3[i];
+    }
+    t.rotmask[0] = 0xf;
+    t.rotmask[1] = 0xf;
+    t.rotmask[2] = C == 2 ? 0x3 : 0x1;  // C = 2: bits 7, 8; C = 3: bit 8
+    return t;
+}
+
 // Pair unit of tile element e: e with the pack bit P removed.
 QS_PHD constexpr unsigned pair_unit(unsigned e, int P) {
     return (e & ((1u << P) - 1u)) | ((e >> (P + 1)) << P);

@@ -15,7 +15,7 @@ cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st) {
     const int64_t groups = L.total_tiles / (L.group > 0 ? L.group : 1);
     if (grid > groups) grid = (int)groups;
     if (grid < 1) grid = 1;
-    if (L.pairc) return launch_sweep_pair(L, grid, st);
+    if (L.pairc) return L.adjoint ? launch_sweep_pair_adj(L, grid, st) : launch_sweep_pair(L, grid, st);
     cudaError_t s = cudaErrorInvalidValue;
     if (L.dtype == 0 && !L.adjoint) sweep_c64f(L.kind, L.variant, false, &L, grid, st, &s);
     else sweep_other(L.dtype, L.adjoint, L.kind, false, &L, grid, st, &s);
@@ -28,7 +28,8 @@ int sweep_grid(int dtype, int adjoint, int kind) {
 }
 
 int pair_choice(int dtype, int adjoint, int kind, int c, int variant) {
-    return (dtype == 0 && !adjoint && kind == 1 && (c == 2 || c == 3) && variant != 0) ? c : 0;
+    if (dtype != 0 || kind != 1 || !(c == 2 || c == 3)) return 0;
+    return (adjoint || variant != 0) ? c : 0;
 }
 
 int sweep_variant(int flags, int nrounds, const SweepRound* rounds) {

@@ -17,6 +17,16 @@ namespace {
 // a * b + c on both halves: one packed f32x2 FMA (fma.rn.f32x2)
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// A zero the compiler cannot see through: XORed into the per-thread shared
+// memory base of a transpose so that the 16-32 slot addresses are formed at
+// the access (one LOP3 each) instead of being hoisted out of the tile loop
+// and held in registers for the whole kernel.
+__device__ __forceinline__ uint32_t opaque_zero() {
+    uint32_t z;
+    asm volatile("mov.u32 %0, 0;" : "=r"(z));
+    return z;
+}
+
 // One 8-byte store of an amplitude whose parts sit in different pairs.  Two
 // 4-byte stores would leave each 32-byte sector half written in between,
 // which costs DRAM reads; the vector store writes whole sectors.
@@ -55,14 +65,14 @@ struct PairSweep {
     template <int g>
     __device__ static __forceinline__ void sts(float4* tb4, const float2 (&X)[NJ], const float2 (&Y)[NJ],
                                                uint32_t tid) {
-        const uint32_t pt = pair_phys(pair_unit(e_thread<g>(tid), P));
+        const uint32_t pt = pair_phys(pair_unit(e_thread<g>(tid), P)) ^ opaque_zero();
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
             tb4[pt ^ pair_phys(pair_unit(e_slot<g>(j), P))] = make_float4(X[j].x, X[j].y, Y[j].x, Y[j].y);
     }
     template <int g>
     __device__ static __forceinline__ void lds(const float4* tb4, float2 (&X)[NJ], float2 (&Y)[NJ], uint32_t tid) {
-        const uint32_t pt = pair_phys(pair_unit(e_thread<g>(tid), P));
+        const uint32_t pt = pair_phys(pair_unit(e_thread<g>(tid), P)) ^ opaque_zero();
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             const float4 v = tb4[pt ^ pair_phys(pair_unit(e_slot<g>(j), P))];

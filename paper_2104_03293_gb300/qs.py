@@ -397,3 +397,33 @@ def _torch_energy_function():
 def energy(gamma, beta, state: State, objective: int = QS_OBJ_ENERGY):
     """Differentiable objective through torch.autograd (gradients from qs_grad)."""
     return _torch_energy_function().apply(gamma, beta, state, objective)
+
+
+def _torch_aqa_function():
+    import torch
+
+    class QSAqa(torch.autograd.Function):
+        """F(tau, s) of the first-order AQA angles (qs_aqa_angles); backward
+        uses qs_grad and the chain rule of qs_aqa_chain."""
+
+        @staticmethod
+        def forward(ctx, tau, s, state, objective=QS_OBJ_ENERGY):
+            t = float(tau.detach().cpu().double())
+            sk = s.detach().cpu().double().numpy()
+            g, b = aqa_angles(t, sk)
+            val, dg, db = state.grad(g, b, objective)
+            dt, ds = aqa_chain(t, sk, dg, db)
+            ctx.save_for_backward(torch.tensor(dt, dtype=tau.dtype), torch.from_numpy(ds).to(s.dtype))
+            return torch.tensor(val, dtype=tau.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dt, ds = ctx.saved_tensors
+            return grad_out * dt, grad_out * ds, None, None
+
+    return QSAqa
+
+
+def aqa_energy(tau, s, state: State, objective: int = QS_OBJ_ENERGY):
+    """Differentiable AQA objective in (tau, schedule knots s_k) through torch.autograd."""
+    return _torch_aqa_function().apply(tau, s, state, objective)

@@ -151,3 +151,13 @@ def pair_unit(e, P):
 
 def pair_phys(u):
     return u ^ ((u >> 3) & 7) ^ ((u >> 6) & 7) ^ ((u >> 9) & 7)
+
+
+def pair_adj_layout(C):
+    if C == 2:
+        return dict(P=2, regs=[[9, 10, 11, 12], [3, 4, 5, 6], [7, 8, 11, 12]],
+                    tbits=[[0, 1, 3, 4, 5, 6, 7, 8], [0, 1, 9, 7, 8, 10, 11, 12], [0, 1, 3, 4, 5, 6, 9, 10]],
+                    rotmask=[0xf, 0xf, 0x3])
+    return dict(P=3, regs=[[9, 10, 11, 12], [4, 5, 6, 7], [8, 10, 11, 12]],
+                tbits=[[0, 1, 2, 4, 5, 6, 7, 8], [0, 1, 2, 8, 9, 10, 11, 12], [0, 1, 2, 4, 5, 6, 7, 9]],
+                rotmask=[0xf, 0xf, 0x1])

@@ -87,3 +87,34 @@ def test_batched_adam_graph_matches_host_adam(qs):
         Er, Pr = oracle.expect(inst, gf[i], bf[i])
         bound = float(np.abs(inst.h).sum() + np.abs(inst.J).sum())
         assert abs(E[i] - Er) <= 1e-5 * max(abs(Er), bound, 1.0) and abs(P[i] - Pr) <= 1e-5
+
+
+def test_autograd_functions_match_the_adjoint(qs):
+    """energy() (free angles) and aqa_energy() (tau and the schedule knots)
+    through torch.autograd against the oracle adjoint and chain rule."""
+    import torch
+    inst = I.erdos_renyi_ising(14, seed=21, h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    st = qs.State(inst.n)
+    st.set_instance(inst)
+    g0, b0 = I.uniform_angles(4, 22)
+    gamma = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
+    beta = torch.tensor(b0, dtype=torch.float64, requires_grad=True)
+    F = qs.energy(gamma, beta, st, qs.QS_OBJ_ENERGY)
+    F.backward()
+    vr, dgr, dbr = oracle.adjoint(inst, g0, b0, 0)
+    scale = max(1.0, np.max(np.abs(np.concatenate([dgr, dbr]))))
+    assert abs(F.item() - vr) <= 1e-5 * max(1.0, abs(vr))
+    assert np.max(np.abs(gamma.grad.numpy() - dgr)) <= 1e-4 * scale
+    assert np.max(np.abs(beta.grad.numpy() - dbr)) <= 1e-4 * scale
+    sk = np.arange(1, 6) / 6.0
+    tau = torch.tensor(0.75, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(sk, dtype=torch.float64, requires_grad=True)
+    P = qs.aqa_energy(tau, s, st, qs.QS_OBJ_GROUND)
+    P.backward()
+    g, b = oracle.aqa_angles(0.75, sk)
+    vr, dgr, dbr = oracle.adjoint(inst, g, b, 1)
+    dt_r, ds_r = oracle.aqa_chain(0.75, sk, dgr, dbr)
+    assert abs(P.item() - vr) <= 1e-5
+    assert abs(tau.grad.item() - dt_r) <= 1e-4 * max(1.0, abs(dt_r))
+    assert np.max(np.abs(s.grad.numpy() - ds_r)) <= 1e-4 * max(1.0, np.max(np.abs(ds_r)))
+    st.close()

@@ -12,7 +12,7 @@ the GPU as an out-of-bounds access.
 import numpy as np
 import pytest
 
-from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_layout,
+from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_adj_layout, pair_layout,
                            pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
 
 
@@ -130,3 +130,33 @@ def test_pair_layouts(C):
             if sh["c"] + sh["n1"] <= 8:
                 shift = sh["g1"] + 8 - sh["c"] - sh["n1"]
                 assert all(tile_to_global(j << 8, sh) == j << shift for j in range(32))
+
+
+@pytest.mark.parametrize("C", [2, 3])
+def test_pair_adjoint_layouts(C):
+    """Adjoint packed-pair layouts (256 threads, 16 pairs per array): each of
+    the three layouts covers the tile once, every target is rotated once per
+    round, the 16-byte transposes are conflict-free per quarter-warp, and the
+    layout-0 store offsets reduce to one shift when the first target run ends
+    below tile bit 9."""
+    L = pair_adj_layout(C)
+    P = L["P"]
+    for g in range(3):
+        regs, tb = L["regs"][g], L["tbits"][g]
+        assert sorted(regs + tb + [P]) == list(range(PAIR_K))
+        es = [sum(((j >> b) & 1) << regs[b] for b in range(4)) for j in range(16)]
+        et = [sum(((t >> i) & 1) << tb[i] for i in range(8)) for t in range(256)]
+        assert len({a | s | (h << P) for a in et for s in es for h in range(2)}) == 1 << PAIR_K
+        for j in range(16):
+            for w0 in range(0, 256, 32):
+                for q in range(0, 32, 8):
+                    banks = {pair_phys(pair_unit(et[w0 + q + l] | es[j], P)) % 8 for l in range(8)}
+                    assert len(banks) == 8, (C, g, j, w0, q)
+    rotated = [P] + [L["regs"][g][b] for g in range(3) for b in range(4) if (L["rotmask"][g] >> b) & 1]
+    assert sorted(rotated) == list(range(C, PAIR_K))
+    assert L["tbits"][0][:2] == [0, 1]  # lanes 0-3 on the carried bits: whole 32-byte runs per store
+    for n in (24, 28, 30, 33, 34):
+        for sh in make_shapes(n, 13, 13, 2, PAGE_BIT["c64"])[1:]:
+            if sh["c"] == C and sh["c"] + sh["n1"] <= 9:
+                shift = sh["g1"] + 9 - sh["c"] - sh["n1"]
+                assert all(tile_to_global(j << 9, sh) == j << shift for j in range(16))
