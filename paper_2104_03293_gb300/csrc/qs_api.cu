@@ -141,8 +141,9 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
     }
     for (size_t s = 0; s < shapes[1].size(); ++s) {
         const Shape& sh = shapes[1][s];
-        if (!pair_choice(dtype, 1, sh.kind, sh.c, 0)) continue;
-        const PairAdjLayout PL = pair_adj_layout(sh.c);
+        const int pc = pair_choice(dtype, 1, sh.kind, sh.c, 0);
+        if (!pc) continue;
+        const PairAdjLayout PL = pair_adj_layout(pc);
         for (int g = 0; g < 3; ++g) {
             int regq[6] = {-1, -1, -1, -1, -1, -1};
             regq[0] = shape_bit(sh, PL.P);  // slot bit 0: the pack bit; bits 1..4: regs[g]

@@ -114,9 +114,9 @@ cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st);
 cudaError_t launch_sweep_pair_adj(const SweepLaunch& L, int grid, cudaStream_t st);
 int sweep_pair_adj_grid();
 int sweep_pair_grid(int variant);  // variant as sweep_variant: 1 phase, 2 rotations only
-// Packed-pair kernel choice for a sweep: the carried-bit count c when the
-// strided complex64 sweep can use it (forward: without readout; adjoint:
-// every reverse sweep), else 0.
+// Packed-pair kernel choice for a sweep, else 0: the carried-bit count c (2
+// or 3) for a strided complex64 sweep (forward: without readout; adjoint:
+// every reverse sweep), 1 for an adjoint sweep of the run-structured shape A.
 int pair_choice(int dtype, int adjoint, int kind, int c, int variant);
 // ---------------------------------------------------------------------------
 // Launch accounting (qs_launch_count): every launcher reports its kernels.

@@ -74,7 +74,9 @@ QS_PHD constexpr PairLayout pair_layout(int C) {
 
 // Adjoint layouts (two arrays, 32 amplitudes = 16 pairs per array and
 // thread, 256 threads): the pack bit plus four register bits per layout and
-// three layouts.  Layout 0 holds the four top tile bits (coalesced stores).
+// three layouts.  Layout 0 holds the four top target bits, so its stores
+// are coalesced over the low tile bits.  C = 2, 3: strided tiles with C
+// carried bits; C = 1: the run-structured shape A.
 struct PairAdjLayout {
     int C, P;
     int regs[3][4];   // tile bit of pair-index bit b (ascending)
@@ -86,6 +88,21 @@ QS_PHD constexpr PairAdjLayout pair_adj_layout(int C) {
     PairAdjLayout t{};
     t.C = C;
     t.P = C;
+    if (C == 1) {
+        // run-structured shape A (targets tile bits [0, 12), batch bit 12):
+        // the pack bit is tile bit 0, so a pair is two adjacent amplitudes
+        t.P = 0;
+        const int r[3][4] = {{8, 9, 10, 11}, {1, 2, 3, 4}, {5, 6, 7, 12}};
+        const int tt[3][8] = {{1, 2, 3, 4, 5, 6, 7, 12}, {5, 6, 7, 8, 9, 10, 11, 12}, {1, 2, 3, 4, 8, 9, 10, 11}};
+        for (int g = 0; g < 3; ++g) {
+            for (int b = 0; b < 4; ++b) t.regs[g][b] = r[g][b];
+            for (int i = 0; i < 8; ++i) t.tbits[g][i] = tt[g][i];
+        }
+        t.rotmask[0] = 0xf;
+        t.rotmask[1] = 0xf;
+        t.rotmask[2] = 0x7;  // bits 5, 6, 7; bit 12 is the batch bit
+        return t;
+    }
     const int r0[4] = {9, 10, 11, 12};
     const int r1c2[4] = {3, 4, 5, 6}, r2c2[4] = {7, 8, 11, 12};
     const int t0c2[8] = {0, 1, 3, 4, 5, 6, 7, 8}, t1c2[8] = {0, 1, 9, 7, 8, 10, 11, 12}, t2c2[8] = {0, 1, 3, 4, 5, 6, 9, 10};

@@ -28,7 +28,9 @@ int sweep_grid(int dtype, int adjoint, int kind) {
 }
 
 int pair_choice(int dtype, int adjoint, int kind, int c, int variant) {
-    if (dtype != 0 || kind != 1 || !(c == 2 || c == 3)) return 0;
+    if (dtype != 0) return 0;
+    if (kind == 0) return (adjoint && c == kRunBits) ? 1 : 0;  // run-structured shape A (adjoint)
+    if (kind != 1 || !(c == 2 || c == 3)) return 0;
     return (adjoint || variant != 0) ? c : 0;
 }
 

@@ -21,6 +21,13 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return _
 // memory base of a transpose so that the 16-32 slot addresses are formed at
 // the access (one LOP3 each) instead of being hoisted out of the tile loop
 // and held in registers for the whole kernel.
+// Landing-buffer position of tile element e: the pack bit flipped with tile
+// bit 4.  The 8-byte reads of layout 0 (half-warp lanes on tile bits 0, 1,
+// 3 or 2, and 4) then hit 16 distinct bank pairs; a 16-byte copy (elements
+// e, e + 1) stays whole because the pack bit is 2 or more.
+template <int P>
+__device__ __forceinline__ uint32_t land(uint32_t e) { return e ^ (((e >> 4) & 1u) << P); }
+
 __device__ __forceinline__ uint32_t opaque_zero() {
     uint32_t z;
     asm volatile("mov.u32 %0, 0;" : "=r"(z));
@@ -86,8 +93,8 @@ struct PairSweep {
         const uint32_t et = e_thread<0>(tid);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const float2 a = src[et | e_slot<0>(j)];
-            const float2 b = src[et | e_slot<0>(j) | (1u << P)];
+            const float2 a = src[land<P>(et | e_slot<0>(j))];
+            const float2 b = src[land<P>(et | e_slot<0>(j) | (1u << P))];
             X[j] = make_float2(a.x, b.x);
             Y[j] = make_float2(a.y, b.y);
         }
@@ -195,7 +202,8 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
         for (int q = tid; q < (1 << K) / 2; q += NT) {
             const uint32_t e = (uint32_t)q * 2;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + e)), "l"(src + tm.gofs(e))
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
+                         "l"(src + tm.gofs(e))
                          : "memory");
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full + b)) : "memory");

@@ -26,6 +26,13 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return _
 // memory base of a transpose so that the 16-32 slot addresses are formed at
 // the access (one LOP3 each) instead of being hoisted out of the tile loop
 // and held in registers for the whole kernel.
+// Landing-buffer position of tile element e: the pack bit flipped with tile
+// bit 4.  The 8-byte reads of layout 0 (half-warp lanes on tile bits 0, 1,
+// 3 or 2, and 4) then hit 16 distinct bank pairs; a 16-byte copy (elements
+// e, e + 1) stays whole because the pack bit is 2 or more.
+template <int P>
+__device__ __forceinline__ uint32_t land(uint32_t e) { return P == 0 ? e : e ^ (((e >> 4) & 1u) << P); }
+
 __device__ __forceinline__ uint32_t opaque_zero() {
     uint32_t z;
     asm volatile("mov.u32 %0, 0;" : "=r"(z));
@@ -45,7 +52,8 @@ __device__ __forceinline__ void warp_sum_f(float v, double* red, int slot, int n
 
 template <int C>
 struct PairAdj {
-    static constexpr int K = kPairK, NT = 256, NJ = 16, P = C, NW = NT / 32, NSLOT = 2 * kMaxRounds;
+    static constexpr int K = kPairK, NT = 256, NJ = 16, P = pair_adj_layout(C).P, NW = NT / 32,
+                         NSLOT = 2 * kMaxRounds;
     static constexpr size_t TILE_BYTES = (size_t)8 << K;
     static constexpr size_t SMEM_BYTES = 3 * TILE_BYTES + 64 + (size_t)NW * NSLOT * 8;
 
@@ -91,10 +99,16 @@ struct PairAdj {
         const uint32_t et = e_thread<0>(tid);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const float2 a = src[et | e_slot<0>(j)];
-            const float2 b = src[et | e_slot<0>(j) | (1u << P)];
-            X[j] = make_float2(a.x, b.x);
-            Y[j] = make_float2(a.y, b.y);
+            if constexpr (P == 0) {  // the two members are adjacent: one 16-byte read
+                const float4 v = reinterpret_cast<const float4*>(src)[(et | e_slot<0>(j)) >> 1];
+                X[j] = make_float2(v.x, v.z);
+                Y[j] = make_float2(v.y, v.w);
+            } else {
+                const float2 a = src[land<P>(et | e_slot<0>(j))];
+                const float2 b = src[land<P>(et | e_slot<0>(j) | (1u << P))];
+                X[j] = make_float2(a.x, b.x);
+                Y[j] = make_float2(a.y, b.y);
+            }
         }
     }
 
@@ -225,7 +239,7 @@ __global__ void __launch_bounds__(256, 1)
             float2* dst = buf + ((size_t)a << K);
             for (int q = tid; q < (1 << K) / 2; q += NT) {
                 const uint32_t e = (uint32_t)q * 2;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + e)),
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + land<P>(e))),
                              "l"(src + tm.gofs(e))
                              : "memory");
             }
@@ -329,37 +343,28 @@ __global__ void __launch_bounds__(256, 1)
         to_layout(0);
 
         if (flags & T_STORE) {
+            // the map is additive over disjoint bits: walk layout 0's pair
+            // index in Gray-code order, one per-bit step per pair
             const uint64_t gP = tm.gofs(1u << P);
-            float2* dp = reinterpret_cast<float2*>(T.psi) + base + tm.gofs(S::template e_thread<0>(tid));
-            float2* dl = reinterpret_cast<float2*>(T.lam) + base + tm.gofs(S::template e_thread<0>(tid));
-            if (T.c + T.n1 <= 9) {  // layout-0 registers (tile bits 9..12) in the second run: one shift
-                const int sh = T.g1 + 9 - T.c - T.n1;
+            const uint64_t t0 = base + tm.gofs(S::template e_thread<0>(tid));
+            float2* dp = reinterpret_cast<float2*>(T.psi) + t0;
+            float2* dl = reinterpret_cast<float2*>(T.lam) + t0;
+            uint64_t step[4];
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) {
-                    const uint64_t o = (uint64_t)j << sh;
-                    stg2(dp + o, Xp[j].x, Yp[j].x);
-                    stg2(dp + o + gP, Xp[j].y, Yp[j].y);
-                    stg2(dl + o, Xl[j].x, Yl[j].x);
-                    stg2(dl + o + gP, Xl[j].y, Yl[j].y);
+            for (int q = 0; q < 4; ++q) step[q] = tm.gofs(1u << pair_adj_layout(C).regs[0][q]);
+            uint64_t o = 0;
+#pragma unroll
+            for (int i = 0; i < NJ; ++i) {
+                const int j = i ^ (i >> 1);
+                if (i > 0) {
+                    const int q = __ffs(i) - 1;
+                    if ((j >> q) & 1) o += step[q];
+                    else o -= step[q];
                 }
-            } else {  // additive map: Gray-code walk over j
-                uint64_t step[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) step[q] = tm.gofs(1u << (9 + q));
-                uint64_t o = 0;
-#pragma unroll
-                for (int i = 0; i < NJ; ++i) {
-                    const int j = i ^ (i >> 1);
-                    if (i > 0) {
-                        const int q = __ffs(i) - 1;
-                        if ((j >> q) & 1) o += step[q];
-                        else o -= step[q];
-                    }
-                    stg2(dp + o, Xp[j].x, Yp[j].x);
-                    stg2(dp + o + gP, Xp[j].y, Yp[j].y);
-                    stg2(dl + o, Xl[j].x, Yl[j].x);
-                    stg2(dl + o + gP, Xl[j].y, Yl[j].y);
-                }
+                stg2(dp + o, Xp[j].x, Yp[j].x);
+                stg2(dp + o + gP, Xp[j].y, Yp[j].y);
+                stg2(dl + o, Xl[j].x, Yl[j].x);
+                stg2(dl + o + gP, Xl[j].y, Yl[j].y);
             }
         }
         if (T.np > 0) {
@@ -391,6 +396,7 @@ static cudaError_t launch_pair_adj_cfg(const SweepLaunch& L, int grid, cudaStrea
 }
 
 cudaError_t launch_sweep_pair_adj(const SweepLaunch& L, int grid, cudaStream_t st) {
+    if (L.pairc == 1) return launch_pair_adj_cfg<1>(L, grid, st);
     if (L.pairc == 2) return launch_pair_adj_cfg<2>(L, grid, st);
     if (L.pairc == 3) return launch_pair_adj_cfg<3>(L, grid, st);
     return cudaErrorInvalidValue;

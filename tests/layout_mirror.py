@@ -154,6 +154,10 @@ def pair_phys(u):
 
 
 def pair_adj_layout(C):
+    if C == 1:  # run-structured shape A: pack bit = tile bit 0
+        return dict(P=0, regs=[[8, 9, 10, 11], [1, 2, 3, 4], [5, 6, 7, 12]],
+                    tbits=[[1, 2, 3, 4, 5, 6, 7, 12], [5, 6, 7, 8, 9, 10, 11, 12], [1, 2, 3, 4, 8, 9, 10, 11]],
+                    rotmask=[0xf, 0xf, 0x7])
     if C == 2:
         return dict(P=2, regs=[[9, 10, 11, 12], [3, 4, 5, 6], [7, 8, 11, 12]],
                     tbits=[[0, 1, 3, 4, 5, 6, 7, 8], [0, 1, 9, 7, 8, 10, 11, 12], [0, 1, 3, 4, 5, 6, 9, 10]],
@@ -161,3 +165,8 @@ def pair_adj_layout(C):
     return dict(P=3, regs=[[9, 10, 11, 12], [4, 5, 6, 7], [8, 10, 11, 12]],
                 tbits=[[0, 1, 2, 4, 5, 6, 7, 8], [0, 1, 2, 8, 9, 10, 11, 12], [0, 1, 2, 4, 5, 6, 7, 9]],
                 rotmask=[0xf, 0xf, 0x1])
+
+
+def land(e, P):
+    """Landing-buffer position of tile element e (packed-pair kernels)."""
+    return e if P == 0 else e ^ (((e >> 4) & 1) << P)

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_adj_layout, pair_layout,
-                           pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
+                           land, pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
 
 
 @pytest.mark.parametrize("key", list(CFG))
@@ -132,7 +132,7 @@ def test_pair_layouts(C):
                 assert all(tile_to_global(j << 8, sh) == j << shift for j in range(32))
 
 
-@pytest.mark.parametrize("C", [2, 3])
+@pytest.mark.parametrize("C", [1, 2, 3])
 def test_pair_adjoint_layouts(C):
     """Adjoint packed-pair layouts (256 threads, 16 pairs per array): each of
     the three layouts covers the tile once, every target is rotated once per
@@ -153,6 +153,12 @@ def test_pair_adjoint_layouts(C):
                     banks = {pair_phys(pair_unit(et[w0 + q + l] | es[j], P)) % 8 for l in range(8)}
                     assert len(banks) == 8, (C, g, j, w0, q)
     rotated = [P] + [L["regs"][g][b] for g in range(3) for b in range(4) if (L["rotmask"][g] >> b) & 1]
+    if C == 1:  # run-structured shape A: targets [0, 12), batch bit 12
+        assert sorted(rotated) == list(range(PAIR_K - 1))
+        # layout-0 lanes on tile bits 1..5: each store instruction covers 32
+        # adjacent pairs; the 16-byte landing reads are conflict-free
+        assert L["tbits"][0][:5] == [1, 2, 3, 4, 5]
+        return
     assert sorted(rotated) == list(range(C, PAIR_K))
     assert L["tbits"][0][:2] == [0, 1]  # lanes 0-3 on the carried bits: whole 32-byte runs per store
     for n in (24, 28, 30, 33, 34):
@@ -160,3 +166,24 @@ def test_pair_adjoint_layouts(C):
             if sh["c"] == C and sh["c"] + sh["n1"] <= 9:
                 shift = sh["g1"] + 9 - sh["c"] - sh["n1"]
                 assert all(tile_to_global(j << 9, sh) == j << shift for j in range(16))
+
+
+@pytest.mark.parametrize("C", [2, 3])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_pair_landing_reads_conflict_free(C, adjoint):
+    """The 8-byte reads of a landed tile into layout 0 hit 16 distinct bank
+    pairs per half-warp, and the landing map keeps every 16-byte copy whole
+    and the tile a bijection."""
+    L = pair_adj_layout(C) if adjoint else pair_layout(C)
+    P, regs, tb = L["P"], L["regs"][0], L["tbits"][0]
+    assert P >= 2
+    nr, ntb = len(regs), len(tb)
+    assert sorted(land(e, P) for e in range(1 << PAIR_K)) == list(range(1 << PAIR_K))
+    assert all(land(e + 1, P) == land(e, P) + 1 for e in range(0, 1 << PAIR_K, 2))
+    et = [sum(((t >> i) & 1) << tb[i] for i in range(ntb)) for t in range(1 << ntb)]
+    for j in range(1 << nr):
+        es = sum(((j >> b) & 1) << regs[b] for b in range(nr))
+        for h in range(2):
+            for w0 in range(0, 1 << ntb, 16):
+                slots = {land(et[w0 + l] | es | (h << P), P) % 16 for l in range(16)}
+                assert len(slots) == 16, (C, adjoint, j, h, w0)
