@@ -162,6 +162,23 @@ int qs_enumerate_noalloc(int n, const double* hfield, int n_edges, const int32_t
                          void* cuda_stream, int64_t* cmin, int64_t* cmax, int64_t* argmin, int64_t* ground_count,
                          int* scale_shift);
 
+/* Tile-shape plan of the handle (the sweeps' "tile width and block shape";
+ * the paper's gate-by-gate engine has no counterpart).
+ *   runs_a  1: shape A is runs of 2^8 amplitudes plus the top four qubits
+ *           (complex64, n >= 24); 0: shape A is 2^13 contiguous amplitudes;
+ *           -1: the default rule (runs from 30 qubits).
+ *   split   index bit from which the strided shapes' qubits are dealt out
+ *           evenly; -1: the default (22 with runs, else the 2 MB page bit).
+ * Re-plans the current Ising cost (same results up to rounding order).
+ * Errors: QS_EINVAL. */
+int qs_set_shape_rule(qs_handle h, int runs_a, int split);
+
+/* Autotuner: time p_trial layers (from |+>, fixed angles) under each
+ * candidate shape plan on this GPU and keep the fastest; reports it (any
+ * pointer may be NULL).  Overwrites the state.  Call after qs_set_ising.
+ * Errors: QS_ESTATE, QS_EINVAL, QS_ECUDA. */
+int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_ms);
+
 /* Gradient of F = <psi_p|O|psi_p> with respect to all 2p angles, where O is
  * H_C (QS_OBJ_ENERGY) or the projector on the minimal-cost states
  * (QS_OBJ_GROUND).  Not in the paper: reverse-mode through the unitary layers,

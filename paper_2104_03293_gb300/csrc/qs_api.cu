@@ -98,7 +98,7 @@ int Uploader::upload(const void* src, size_t bytes, cudaStream_t st) {
 // Instance: validated Ising + device cost programs + ground-state data.
 // ---------------------------------------------------------------------------
 int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_edges, const int32_t* edges,
-                  const double* J, cudaStream_t st, DevBuf& enum_scratch) {
+                  const double* J, cudaStream_t st, DevBuf& enum_scratch, ShapeRule rule) {
     IsingInt I;
     std::string err;
     int rc = validate_ising(n_, hfield, n_edges, edges, J, I, err);
@@ -119,7 +119,7 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
     };
     for (int cfgi = 0; cfgi < 2; ++cfgi) {
         const KernelCfg cfg = kernel_cfg(dtype, cfgi == 1);
-        shapes[cfgi] = make_shapes(nphys, cfg, page_bit_for(dtype));
+        shapes[cfgi] = make_shapes(nphys, cfg, page_bit_for(dtype), rule);
         for (size_t s = 0; s < shapes[cfgi].size(); ++s)
             for (int g = 0; g < kMaxLayouts; ++g) {
                 if (g >= num_layouts(shapes[cfgi][s], cfg.R)) { prog_off[cfgi][s][g] = prog_off[cfgi][s][0]; continue; }
@@ -213,6 +213,9 @@ struct qs_state {
     bool have_readout = false;
     int grid[2][5] = {};  // [adjoint][kernel kind; 3, 4 = packed-pair kernel, phase / lean]
     int device = 0;
+    ShapeRule rule;                      // tile-shape plan (qs_set_shape_rule / qs_autotune)
+    std::vector<double> ising_h, ising_J;  // the last qs_set_ising input, to re-plan
+    std::vector<int32_t> ising_e;
 };
 
 static int check_handle(qs_handle h) {
@@ -303,9 +306,76 @@ int qs_set_path(qs_handle h, int path) {
 int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* edges, const double* J) {
     if (int rc = check_handle(h)) return rc;
     Instance tmp;
-    if (int rc = tmp.set(h->n, h->nphys, h->dtype, hfield, n_edges, edges, J, h->st, h->enum_scratch)) return rc;
+    if (int rc = tmp.set(h->n, h->nphys, h->dtype, hfield, n_edges, edges, J, h->st, h->enum_scratch, h->rule))
+        return rc;
     h->inst = std::move(tmp);
     h->have_readout = false;
+    h->ising_h.assign(hfield, hfield + h->n);
+    h->ising_e.assign(edges, edges + 2 * (size_t)n_edges);
+    h->ising_J.assign(J, J + n_edges);
+    return QS_OK;
+}
+
+// Rebuild the instance's shapes and cost programs under h->rule.
+static int replan(qs_handle h) {
+    if (!h->inst.valid) return QS_OK;
+    Instance tmp;
+    const int m = (int)h->ising_J.size();
+    if (int rc = tmp.set(h->n, h->nphys, h->dtype, h->ising_h.data(), m, h->ising_e.data(), h->ising_J.data(), h->st,
+                         h->enum_scratch, h->rule))
+        return rc;
+    h->inst = std::move(tmp);
+    h->have_readout = false;
+    return QS_OK;
+}
+
+int qs_set_shape_rule(qs_handle h, int runs_a, int split) {
+    if (int rc = check_handle(h)) return rc;
+    if (runs_a < -1 || runs_a > 1 || split < -1 || split >= h->nphys + 1)
+        return set_error(QS_EINVAL, "qs_set_shape_rule: runs_a in {-1, 0, 1}, split in [-1, n]");
+    h->rule = ShapeRule{runs_a, split};
+    return replan(h);
+}
+
+int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_ms) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->inst.valid) return set_error(QS_ESTATE, "qs_autotune: call qs_set_ising first");
+    if (p_trial < 1 || p_trial > 64) return set_error(QS_EINVAL, "qs_autotune: p_trial outside [1, 64]");
+    // candidates: contiguous shape A with the page-bit split, and (complex64,
+    // 24 qubits and more) the run-structured A with three split bits
+    std::vector<ShapeRule> cand{ShapeRule{0, page_bit_for(h->dtype)}};
+    if (h->dtype == QS_C64 && h->nphys >= 24)
+        for (int sp : {20, 22, 24}) cand.push_back(ShapeRule{1, sp});
+    std::vector<double> g(p_trial, 0.3), b(p_trial, 0.7);
+    const ShapeRule keep = h->rule;
+    double best = 1e300;
+    ShapeRule pick = cand[0];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) return cuda_error(ce, "qs_autotune: events");
+    int rc = QS_OK;
+    for (const ShapeRule& r : cand) {
+        h->rule = r;
+        if ((rc = replan(h))) break;
+        if ((rc = qs_evolve(h, p_trial, g.data(), b.data(), 1))) break;  // warm-up
+        cudaEventRecord(e0, h->st);
+        if ((rc = qs_evolve(h, p_trial, g.data(), b.data(), 1))) break;
+        cudaEventRecord(e1, h->st);
+        ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) { rc = cuda_error(ce, "qs_autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = r; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->rule = rc ? keep : pick;
+    if (int rc2 = replan(h)) return rc ? rc : rc2;
+    if (rc) return rc;
+    if (runs_a) *runs_a = pick.runs_a;
+    if (split) *split = pick.split;
+    if (best_ms) *best_ms = best;
     return QS_OK;
 }
 
@@ -692,7 +762,7 @@ int qs_canonicalize(qs_handle h) {
 int qs_plan_info(qs_handle h, int p, int* tile_shapes, int* sweeps) {
     if (!h) return set_error(QS_EINVAL, "NULL handle");
     if (p < 0) return set_error(QS_EINVAL, "p < 0");
-    const auto sh = make_shapes(h->nphys, kernel_cfg(h->dtype, false), page_bit_for(h->dtype));
+    const auto sh = make_shapes(h->nphys, kernel_cfg(h->dtype, false), page_bit_for(h->dtype), h->rule);
     if (tile_shapes) *tile_shapes = (int)sh.size();
     if (sweeps) *sweeps = (int)plan_forward((int)sh.size(), p, true).size();
     return QS_OK;

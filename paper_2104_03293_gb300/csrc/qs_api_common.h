@@ -64,7 +64,7 @@ struct Instance {
     DevBuf progs;
     const int32_t* prog(size_t off) const { return reinterpret_cast<const int32_t*>(progs.ptr) + off; }
     int set(int n, int nphys, int dtype, const double* hfield, int n_edges, const int32_t* edges, const double* J,
-            cudaStream_t st, DevBuf& enum_scratch);
+            cudaStream_t st, DevBuf& enum_scratch, ShapeRule rule = ShapeRule{});
 };
 
 }  // namespace qs

@@ -146,14 +146,15 @@ int validate_ising(int n, const double* hfield, int n_edges, const int32_t* edge
 // a different page: a tile with t such targets touches 2^t pages at once.  The
 // qubits between K_A - 1 and the page bit are therefore dealt out evenly, one
 // low run per strided shape, and each shape fills up with a high run.
-std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit) {
+std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, ShapeRule rule) {
     std::vector<Shape> v;
     Shape a;
     a.K = cfg.K_A; a.c = 0; a.g0 = 0; a.nt = cfg.K_A - 1; a.kind = 0; a.n1 = 0; a.g1 = 0;
     a.ntiles = (int64_t)1 << (nphys - cfg.K_A);
     // strided shapes cover qubits [lo, hi); bits from `split` up are dealt out
-    int lo = cfg.K_A - 1, hi = nphys, split = page_bit;
-    if (cfg.K_A == 13 && cfg.K_B == 13 && nphys >= 30) {
+    int lo = cfg.K_A - 1, hi = nphys, split = rule.split >= 0 ? rule.split : page_bit;
+    const bool runs_ok = cfg.K_A == 13 && cfg.K_B == 13 && nphys >= 2 * cfg.K_A - 2;
+    if (runs_ok && (rule.runs_a == 1 || (rule.runs_a < 0 && nphys >= 30))) {
         // complex64, largest states: shape A = runs of 2^8 amplitudes (2 KB)
         // with targets [0, 8) and the top four qubits, batch bit 8; the far
         // bits left go evenly to the strided shapes
@@ -164,7 +165,7 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit) {
         a.g1 = a.c;
         lo = a.c;
         hi = nphys - f;
-        split = kFarBitC64;
+        split = rule.split >= 0 ? rule.split : kFarBitC64;
         // the sweep kernel relies on this structure (tile index = bits
         // [kRunBits + 1, nphys - f), i.e. base = tile << (kRunBits + 1))
         if (a.g0 + a.n1 != nphys || a.g1 != kRunBits || a.c + a.n1 + 1 != cfg.K_A) return {};

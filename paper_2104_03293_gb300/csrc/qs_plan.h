@@ -57,7 +57,16 @@ struct PlanSweep {
 
 // Index bit at which a new 2 MB page starts (complex64: 8-byte amplitudes).
 inline int page_bit_for(int dtype) { return dtype == 0 ? 18 : 17; }
-std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit);
+// Shape-plan choice (set by the autotuner or the caller): runs_a = 1 makes
+// shape A run-structured (complex64, K = 13), 0 contiguous, -1 the default
+// rule (run-structured from 30 qubits); split = index bit from which the
+// strided shapes' qubits are dealt out evenly, -1 = default (bit 22 with a
+// run-structured A, else the 2 MB page bit).
+struct ShapeRule {
+    int runs_a = -1;
+    int split = -1;
+};
+std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, ShapeRule rule = ShapeRule{});
 void shape_regq(const Shape& s, int R, int g, int* regq);
 int num_layouts(const Shape& s, int R);
 std::vector<PlanSweep> plan_forward(int S, int p, bool gen);

@@ -55,6 +55,8 @@ _SIGS = {
     "qs_readout": [_P, _PD, _PD, _PD],
     "qs_cost_info": [_P, _PI64, _PI64, _PI64, _PI64, _PI],
     "qs_enumerate_noalloc": [_I, _PD, _I, _PI32, _PD, _P, _PI64, _PI64, _PI64, _PI64, _PI],
+    "qs_set_shape_rule": [_P, _I, _I],
+    "qs_autotune": [_P, _I, _PI, _PI, _PD],
     "qs_grad": [_P, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "qs_set_adjoint_buffer": [_P, _P, ctypes.c_size_t],
     "qs_copy_state": [_P, _P, ctypes.c_size_t],
@@ -206,6 +208,15 @@ class State:
         s = ctypes.c_int()
         _check(lib().qs_cost_info(self._h, *[ctypes.byref(v) for v in vals], ctypes.byref(s)))
         return tuple(v.value for v in vals) + (s.value,)
+
+    def set_shape_rule(self, runs_a: int = -1, split: int = -1):
+        _check(lib().qs_set_shape_rule(self._h, int(runs_a), int(split)))
+
+    def autotune(self, p_trial: int = 2):
+        """Time the candidate tile-shape plans, keep the fastest: (runs_a, split, ms)."""
+        r, sp, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().qs_autotune(self._h, int(p_trial), ctypes.byref(r), ctypes.byref(sp), ctypes.byref(ms)))
+        return r.value, sp.value, ms.value
 
     def set_adjoint_buffer(self, buffer):
         self._adj = buffer

@@ -155,3 +155,30 @@ def test_flat_cost_and_fields_only(qs):
     ref = oracle.evolve(inst, g, b)
     assert np.linalg.norm(st.copy_state() - ref) <= 1e-4
     st.close()
+
+
+def test_shape_rules_and_autotuner(qs):
+    """Every candidate shape plan gives the oracle's state (n = 24: strided,
+    packed-pair and run-structured shapes), and the autotuner keeps one of
+    them and still matches."""
+    inst = I.erdos_renyi_ising(24, I.workload_seed(5, 200), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    g, b = _angles(3)
+    ref = oracle.evolve(inst, g, b)
+    Er, Pr, _ = oracle.readout(inst, ref)
+    st = qs.State(inst.n)
+    st.set_instance(inst)
+    for rule in [(0, 18), (1, 20), (1, 22), (1, 24), (-1, -1)]:
+        st.set_shape_rule(*rule)
+        st.evolve(g, b)
+        E, P, _ = st.readout()
+        assert np.linalg.norm(st.copy_state() - ref) <= 1e-4, rule
+        assert abs(E - Er) <= 1e-5 * max(abs(Er), 1.0) and abs(P - Pr) <= 1e-5
+    ra, sp, ms = st.autotune(2)
+    assert (ra, sp) in [(0, 18), (1, 20), (1, 22), (1, 24)] and ms > 0
+    st.evolve(g, b)
+    assert np.linalg.norm(st.copy_state() - ref) <= 1e-4
+    v, dg, db = st.grad(g, b, 1)
+    vr, dgr, dbr = oracle.adjoint(inst, g, b, 1)
+    scale = max(1.0, float(np.abs(np.concatenate([dgr, dbr])).max()))
+    assert abs(v - vr) <= 1e-5 and np.abs(dg - dgr).max() <= 1e-4 * scale
+    st.close()
