@@ -166,7 +166,7 @@ int qs_enumerate_noalloc(int n, const double* hfield, int n_edges, const int32_t
  * the paper's gate-by-gate engine has no counterpart).
  *   runs_a  1: shape A is runs of 2^8 amplitudes plus the top four qubits
  *           (complex64, n >= 24); 0: shape A is 2^13 contiguous amplitudes;
- *           -1: the default rule (runs from 30 qubits).
+ *           -1: the default rule (runs from 33 qubits).
  *   split   index bit from which the strided shapes' qubits are dealt out
  *           evenly; -1: the default (22 with runs, else the 2 MB page bit).
  * Re-plans the current Ising cost (same results up to rounding order).

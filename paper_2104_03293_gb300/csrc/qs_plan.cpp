@@ -154,7 +154,7 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, Sh
     // strided shapes cover qubits [lo, hi); bits from `split` up are dealt out
     int lo = cfg.K_A - 1, hi = nphys, split = rule.split >= 0 ? rule.split : page_bit;
     const bool runs_ok = cfg.K_A == 13 && cfg.K_B == 13 && nphys >= 2 * cfg.K_A - 2;
-    if (runs_ok && (rule.runs_a == 1 || (rule.runs_a < 0 && nphys >= 30))) {
+    if (runs_ok && (rule.runs_a == 1 || (rule.runs_a < 0 && nphys >= 33))) {
         // complex64, largest states: shape A = runs of 2^8 amplitudes (2 KB)
         // with targets [0, 8) and the top four qubits, batch bit 8; the far
         // bits left go evenly to the strided shapes

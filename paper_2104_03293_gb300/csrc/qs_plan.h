@@ -59,7 +59,7 @@ struct PlanSweep {
 inline int page_bit_for(int dtype) { return dtype == 0 ? 18 : 17; }
 // Shape-plan choice (set by the autotuner or the caller): runs_a = 1 makes
 // shape A run-structured (complex64, K = 13), 0 contiguous, -1 the default
-// rule (run-structured from 30 qubits); split = index bit from which the
+// rule (run-structured from 33 qubits); split = index bit from which the
 // strided shapes' qubits are dealt out evenly, -1 = default (bit 22 with a
 // run-structured A, else the 2 MB page bit).
 struct ShapeRule {

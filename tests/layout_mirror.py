@@ -42,7 +42,7 @@ FAR_BIT_C64 = 22
 def make_shapes(nphys, KA, KB, cmin, page_bit=18):
     a = dict(K=KA, c=0, g0=0, nt=KA - 1, kind=0, n1=0, g1=0)
     lo, hi, split = KA - 1, nphys, page_bit
-    if KA == 13 and KB == 13 and nphys >= 30:
+    if KA == 13 and KB == 13 and nphys >= 33:
         f = 4
         a.update(c=KA - 1 - f, g0=nphys - f, n1=f, g1=KA - 1 - f)
         lo, hi, split = a["c"], nphys - f, FAR_BIT_C64

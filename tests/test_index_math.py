@@ -32,7 +32,7 @@ def test_every_sweep_is_a_bijection(key):
             owned += [gbit(tb, sh) for tb in range(sh["K"] - 1 if sh["kind"] == 0 else sh["K"])
                       if sh["kind"] == 0 or tb >= sh["c"]]
         assert sorted(owned) == list(range(nphys))
-        if nphys >= 30 and key[0] == "c64":
+        if nphys >= 33 and key[0] == "c64":
             # the largest states spread the far bits: shape A takes the top
             # four qubits (2 KB runs), the strided shapes at most four each
             assert shapes[0]["c"] == 8 and owned[8:12] == list(range(nphys - 4, nphys))
