@@ -16,7 +16,8 @@ amplitudes, (n + 1) 2^n updates.  Inputs (instance, angles) come from host
 arrays every step; the state never leaves HBM.
 
 --impl reference times the CPU oracle (complex128, gate by gate) on the host
-cores on a bounded sample of the same workload family.
+cores on a bounded sample of the same workload family: one layer at n = 26
+per step (the n = 34 state does not fit host memory in complex128).
 """
 from __future__ import annotations
 

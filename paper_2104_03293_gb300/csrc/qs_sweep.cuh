@@ -6,11 +6,12 @@
 // 2^n diagonal), the readout (<H_C>, ground probability, norm) and the adjoint
 // accumulations fused in.
 //
-// Persistent CTAs (two per SM for the forward sweep) walk over tiles of 2^K
-// amplitudes:
+// Persistent CTAs (two per SM for the forward sweep, one for the adjoint) walk
+// over tiles of 2^K amplitudes:
 //   * a tile lands in the CTA's shared-memory tile buffer: one bulk copy
-//     (cp.async.bulk, TMA) for a contiguous tile, per-thread 16-byte
-//     cp.async copies for a strided one (runs of 2^c amplitudes); both
+//     (cp.async.bulk, TMA) for a contiguous tile, one per 2 KB run (warp 0)
+//     for a run-structured one (kind 2), per-thread 16-byte cp.async copies
+//     for a strided one (runs of 2^c amplitudes); all
 //     complete on an mbarrier, with bounded waits.  The load of the next tile
 //     is issued as soon as the current one has been read for the last time,
 //     so it overlaps the tile's remaining work and the other CTA.

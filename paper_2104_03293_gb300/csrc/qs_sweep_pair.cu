@@ -1,8 +1,9 @@
 // Packed-pair sweep: the strided complex64 forward sweeps (rotations only, or
 // rotations with a layer boundary and its phase), layouts in qs_pair.h.
 //
-// Same tile walk as sweep_kernel (qs_sweep.cuh): persistent CTAs, two per SM,
-// one in-place 64 KB tile buffer, 16-byte cp.async copies of the strided tile
+// Same tile walk as sweep_kernel (qs_sweep.cuh): persistent CTAs, three per SM
+// (registers bounded to 168 per thread), each with one in-place 64 KB tile
+// buffer, 16-byte cp.async copies of the strided tile
 // completing on an mbarrier (bounded wait), the next tile's copies issued
 // after the current tile's last shared-memory read.  The difference is the
 // register format: pairs split by component and updated with packed f32x2
@@ -154,9 +155,9 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Two CTAs per SM, each with NB = 1 in-place tile buffer: after tile k's last
-// shared-memory read the buffer takes tile k + 1 (NB > 1 would keep more
-// tiles in flight per CTA, at one CTA per SM; measured slower).
+// Three CTAs per SM, each with NB = 1 in-place tile buffer: after tile k's
+// last shared-memory read the buffer takes tile k + 1 (NB > 1 would keep
+// more tiles in flight per CTA, at one CTA per SM; measured slower).
 //
 // CL = 4: clusters of four CTAs take the four tiles that differ in tile-index
 // bits 0 and 1 (the neighbouring runs of one 128-byte line when c = 2) and
@@ -164,8 +165,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 // share are fetched once.  Every CTA of a cluster walks the same number of
 // tiles (the tile count and the grid are multiples of four) and passes the
 // barrier once per tile, also after a timed-out wait.
-// Rotation-only sweeps hold fewer live values and fit three CTAs per SM.
-template <int V> struct PairOcc { static constexpr int value = 3; };
+template <int V> struct PairOcc { static constexpr int value = 3; };  // CTAs per SM (both variants)
 
 template <int C, int V, int CL>
 __global__ void __launch_bounds__(128, PairOcc<V>::value)
