@@ -167,6 +167,37 @@ struct PairAdj {
         }
     }
 
+    // both arrays from layout g: the map is additive over disjoint bits, so
+    // the pair index is walked in Gray-code order, one per-bit step per pair
+    template <int g>
+    __device__ static __forceinline__ void store(float2* psi, float2* lam, const TMap& tm, uint64_t base,
+                                                 const float2 (&Xp)[NJ], const float2 (&Yp)[NJ],
+                                                 const float2 (&Xl)[NJ], const float2 (&Yl)[NJ], uint32_t tid) {
+        const uint64_t gP = tm.gofs(1u << P);
+        const uint64_t t0 = base + tm.gofs(e_thread<g>(tid));
+        float2* dp = psi + t0;
+        float2* dl = lam + t0;
+        uint64_t step[4];
+        static_for<0, 4>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            step[q] = tm.gofs(1u << pair_adj_layout(C).regs[g][q]);
+        });
+        uint64_t o = 0;
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            const int j = i ^ (i >> 1);
+            if (i > 0) {
+                const int q = __ffs(i) - 1;
+                if ((j >> q) & 1) o += step[q];
+                else o -= step[q];
+            }
+            stg2(dp + o, Xp[j].x, Yp[j].x);
+            stg2(dp + o + gP, Xp[j].y, Yp[j].y);
+            stg2(dl + o, Xl[j].x, Yl[j].x);
+            stg2(dl + o + gP, Xl[j].y, Yl[j].y);
+        }
+    }
+
     // phase of the layer on both arrays, then the dF/dgamma term C Im(conj(l) p)
     // (slot m = half | j << 1 of the layout's cost program)
     template <int g>
@@ -340,32 +371,14 @@ __global__ void __launch_bounds__(256, 1)
             warp_sum_f(gB, red, 2 * r, NSLOT);
             warp_sum_f(gG, red, 2 * r + 1, NSLOT);
         }
-        to_layout(0);
-
+        // stored from the layout the rounds end in: 0 after an even number,
+        // 2 after an odd one (both hold adjacent amplitudes on the low lanes)
+        if (cur == 1) to_layout(0);
         if (flags & T_STORE) {
-            // the map is additive over disjoint bits: walk layout 0's pair
-            // index in Gray-code order, one per-bit step per pair
-            const uint64_t gP = tm.gofs(1u << P);
-            const uint64_t t0 = base + tm.gofs(S::template e_thread<0>(tid));
-            float2* dp = reinterpret_cast<float2*>(T.psi) + t0;
-            float2* dl = reinterpret_cast<float2*>(T.lam) + t0;
-            uint64_t step[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) step[q] = tm.gofs(1u << pair_adj_layout(C).regs[0][q]);
-            uint64_t o = 0;
-#pragma unroll
-            for (int i = 0; i < NJ; ++i) {
-                const int j = i ^ (i >> 1);
-                if (i > 0) {
-                    const int q = __ffs(i) - 1;
-                    if ((j >> q) & 1) o += step[q];
-                    else o -= step[q];
-                }
-                stg2(dp + o, Xp[j].x, Yp[j].x);
-                stg2(dp + o + gP, Xp[j].y, Yp[j].y);
-                stg2(dl + o, Xl[j].x, Yl[j].x);
-                stg2(dl + o + gP, Xl[j].y, Yl[j].y);
-            }
+            float2* psi = reinterpret_cast<float2*>(T.psi);
+            float2* lam = reinterpret_cast<float2*>(T.lam);
+            if (cur == 0) S::template store<0>(psi, lam, tm, base, Xp, Yp, Xl, Yl, tid);
+            else S::template store<2>(psi, lam, tm, base, Xp, Yp, Xl, Yl, tid);
         }
         if (T.np > 0) {
             const int np = T.np;
