@@ -22,12 +22,17 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return _
 // memory base of a transpose so that the 16-32 slot addresses are formed at
 // the access (one LOP3 each) instead of being hoisted out of the tile loop
 // and held in registers for the whole kernel.
-// Landing-buffer position of tile element e: the pack bit flipped with tile
-// bit 4.  The 8-byte reads of layout 0 (half-warp lanes on tile bits 0, 1,
-// 3 or 2, and 4) then hit 16 distinct bank pairs; a 16-byte copy (elements
-// e, e + 1) stays whole because the pack bit is 2 or more.
+// Landing-buffer position of tile element e: the pack bit P flipped with
+// tile bits 4 and 8 (and, for P = 2, bit 3 with tile bit 9).  A tile is read
+// from the landing buffer into layout 0 or layout 1; the 8-byte reads of
+// either (half-warp lanes on tile bits 0, 1 and 3, 4 or 9, 8 when P = 2;
+// 0, 1, 2 and 4 or 8 when P = 3) then hit 16 distinct bank pairs, and a
+// 16-byte copy (elements e, e + 1) stays whole because bit 0 is kept.
 template <int P>
-__device__ __forceinline__ uint32_t land(uint32_t e) { return e ^ (((e >> 4) & 1u) << P); }
+__device__ __forceinline__ uint32_t land(uint32_t e) {
+    const uint32_t f = ((e >> 4) ^ (e >> 8)) & 1u;
+    return P == 2 ? e ^ (f << 2) ^ (((e >> 9) & 1u) << 3) : e ^ (f << P);
+}
 
 __device__ __forceinline__ uint32_t opaque_zero() {
     uint32_t z;
@@ -88,14 +93,15 @@ struct PairSweep {
             Y[j] = make_float2(v.z, v.w);
         }
     }
-    // from the landing buffer (tile order, one float2 per amplitude) into layout 0
+    // from the landing buffer (tile order, one float2 per amplitude) into layout g
+    template <int g>
     __device__ static __forceinline__ void lds_dense(const float2* src, float2 (&X)[NJ], float2 (&Y)[NJ],
                                                      uint32_t tid) {
-        const uint32_t et = e_thread<0>(tid);
+        const uint32_t et = e_thread<g>(tid);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const float2 a = src[land<P>(et | e_slot<0>(j))];
-            const float2 b = src[land<P>(et | e_slot<0>(j) | (1u << P))];
+            const float2 a = src[land<P>(et | e_slot<g>(j))];
+            const float2 b = src[land<P>(et | e_slot<g>(j) | (1u << P))];
             X[j] = make_float2(a.x, b.x);
             Y[j] = make_float2(a.y, b.y);
         }
@@ -232,8 +238,11 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         const int64_t nx = gt + (int64_t)NB * gridDim.x;
         float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
         float4* buf4 = reinterpret_cast<float4*>(buf);
-        // transposes of this tile: one per round, plus one back to layout 0
-        const int ntr = nr + (nr & 1);
+        // a tile is read into layout 1 for an odd number of rounds and into
+        // layout 0 for an even one; each round moves once to the other layout,
+        // so the tile ends in layout 0 (its coalesced stores) after nr
+        // transposes
+        const int ntr = nr;
         int done_tr = 0;
         auto release = [&]() {
             if (CL > 1) cluster_sync_all();
@@ -255,10 +264,12 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         }
         phase ^= 1u << b;
         pend &= ~(1u << b);
-        S::lds_dense(buf, X, Y, tid);
+        int cur = nr & 1;
+        if (cur) S::template lds_dense<1>(buf, X, Y, tid);
+        else S::template lds_dense<0>(buf, X, Y, tid);
         __syncthreads();  // dense reads done before the swizzled writes
+        if (ntr == 0) release();
 
-        int cur = 0;
         auto to_layout = [&](int g) {
             if (g == cur) return;
             if (cur == 0) S::template sts<0>(buf4, X, Y, tid);

@@ -168,5 +168,12 @@ def pair_adj_layout(C):
 
 
 def land(e, P):
-    """Landing-buffer position of tile element e (packed-pair kernels)."""
+    """Landing-buffer position of tile element e (packed-pair adjoint)."""
     return e if P == 0 else e ^ (((e >> 4) & 1) << P)
+
+
+def land_fwd(e, P):
+    """Landing-buffer position of tile element e (packed-pair forward: read
+    into layout 0 or layout 1)."""
+    f = ((e >> 4) ^ (e >> 8)) & 1
+    return e ^ (f << 2) ^ (((e >> 9) & 1) << 3) if P == 2 else e ^ (f << P)

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_adj_layout, pair_layout,
-                           land, pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
+                           land, land_fwd, pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
 
 
 @pytest.mark.parametrize("key", list(CFG))
@@ -169,19 +169,26 @@ def test_pair_adjoint_layouts(C):
 @pytest.mark.parametrize("C", [2, 3])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_pair_landing_reads_conflict_free(C, adjoint):
-    """The 8-byte reads of a landed tile into layout 0 hit 16 distinct bank
-    pairs per half-warp, and the landing map keeps every 16-byte copy whole
-    and the tile a bijection."""
+    """The 8-byte reads of a landed tile into the layouts it is read into
+    (layout 0; the forward also layout 1, for an odd number of rounds) hit 16
+    distinct bank pairs per half-warp, and the landing map keeps every
+    16-byte copy whole, the tile a bijection and the copies of a
+    quarter-warp on distinct 16-byte bank groups."""
     L = pair_adj_layout(C) if adjoint else pair_layout(C)
-    P, regs, tb = L["P"], L["regs"][0], L["tbits"][0]
+    lf = land if adjoint else land_fwd
+    P = L["P"]
     assert P >= 2
-    nr, ntb = len(regs), len(tb)
-    assert sorted(land(e, P) for e in range(1 << PAIR_K)) == list(range(1 << PAIR_K))
-    assert all(land(e + 1, P) == land(e, P) + 1 for e in range(0, 1 << PAIR_K, 2))
-    et = [sum(((t >> i) & 1) << tb[i] for i in range(ntb)) for t in range(1 << ntb)]
-    for j in range(1 << nr):
-        es = sum(((j >> b) & 1) << regs[b] for b in range(nr))
-        for h in range(2):
-            for w0 in range(0, 1 << ntb, 16):
-                slots = {land(et[w0 + l] | es | (h << P), P) % 16 for l in range(16)}
-                assert len(slots) == 16, (C, adjoint, j, h, w0)
+    assert sorted(lf(e, P) for e in range(1 << PAIR_K)) == list(range(1 << PAIR_K))
+    assert all(lf(e + 1, P) == lf(e, P) + 1 for e in range(0, 1 << PAIR_K, 2))
+    for q0 in range(0, 1 << (PAIR_K - 1), 8):  # cp.async copies: element 2 q per thread
+        assert len({(lf(2 * q, P) >> 1) % 8 for q in range(q0, q0 + 8)}) == 8
+    for g in ((0,) if adjoint else (0, 1)):
+        regs, tb = L["regs"][g], L["tbits"][g]
+        nr, ntb = len(regs), len(tb)
+        et = [sum(((t >> i) & 1) << tb[i] for i in range(ntb)) for t in range(1 << ntb)]
+        for j in range(1 << nr):
+            es = sum(((j >> b) & 1) << regs[b] for b in range(nr))
+            for h in range(2):
+                for w0 in range(0, 1 << ntb, 16):
+                    slots = {lf(et[w0 + l] | es | (h << P), P) % 16 for l in range(16)}
+                    assert len(slots) == 16, (C, adjoint, g, j, h, w0)
