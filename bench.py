@@ -157,7 +157,8 @@ def secondary_workloads(qs, I, torch):
     batched forwards of 512 uneven instances against the same instances one
     at a time (tiled and plain per-gate launches); the n=26 p=10 gradient
     against a forward and against 4p plain forwards (central differences);
-    64 instances x 200 Adam steps replayed from a CUDA graph."""
+    64 instances x 200 Adam steps replayed from a CUDA graph; the p = 1
+    landscape of one n = 18 instance on a 64 x 64 angle grid."""
     import numpy as np
     out = {}
 
@@ -237,6 +238,24 @@ def secondary_workloads(qs, I, torch):
     t_adam = 1e3 * (time.perf_counter() - t0)
     bt.close()
     out["adam_64x200"] = {"ms": t_adam, "mean_E": float(np.mean(E)), "mean_P_ground": float(np.mean(P))}
+    # p = 1 landscape: 64 x 64 (gamma, beta) grid of one n = 18 instance
+    inst = I.erdos_renyi_ising(18, I.workload_seed(6, 2), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    gam = np.arange(64) * (2 * np.pi / 64)
+    bet = np.arange(64) * (np.pi / 64)
+    t0 = time.perf_counter()
+    E, P, bt = qs.grid_scan(inst.h, inst.edges, inst.J, gam, bet, return_batch=True)
+    t_setup = time.perf_counter() - t0
+    gg, bb = np.repeat(gam, 64).reshape(-1, 1), np.tile(bet, 64).reshape(-1, 1)
+
+    def run_grid():
+        bt.evolve(gg, bb)
+        bt.results()
+    t_grid = timed(run_grid, 3)
+    bt.close()
+    out["grid_64x64_n18"] = {"evolve_ms": t_grid, "first_call_s": t_setup,
+                             "points_per_s": 4096 / (t_grid / 1e3),
+                             "amplitude_updates_per_s": 4096 * 19 * 2 ** 18 / (t_grid / 1e3),
+                             "min_E": float(E.min()), "max_P_ground": float(P.max())}
     return out
 
 

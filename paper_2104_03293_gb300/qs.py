@@ -383,6 +383,36 @@ class Batch:
         return self._split(g), self._split(b)
 
 
+def grid_scan(h, edges, J, gammas, betas, stream=None, return_batch: bool = False):
+    """p = 1 landscapes of one instance over a (gamma, beta) grid (the
+    energy and success-probability maps of Sec. 3.2.1, Fig. 4, scanned there
+    on 64 x 64 points, beta in [0, pi), gamma in [0, 2 pi)): E and
+    P_ground at every point of gammas x betas, from one batched evolve of
+    len(gammas) * len(betas) copies of the instance (qs_batch_*), each copy
+    with its own p = 1 angles.  Returns two arrays of shape (len(gammas),
+    len(betas)); with return_batch, also the evolved Batch (caller closes it).
+    Every copy holds its own cost program (built by qs_batch_set_ising)."""
+    h = _f64(h)
+    gammas = np.asarray(gammas, dtype=np.float64).ravel()
+    betas = np.asarray(betas, dtype=np.float64).ravel()
+    G, B = gammas.size, betas.size
+    if G == 0 or B == 0:
+        raise QSError(QS_EINVAL, "grid_scan: empty angle grid")
+    bt = Batch([h.size] * (G * B), stream=stream)
+    try:
+        for i in range(G * B):
+            bt.set_ising(i, h, edges, J)
+        bt.evolve(np.repeat(gammas, B).reshape(-1, 1), np.tile(betas, G).reshape(-1, 1))
+        E, P = bt.results()
+    except BaseException:
+        bt.close()
+        raise
+    if return_batch:
+        return E.reshape(G, B), P.reshape(G, B), bt
+    bt.close()
+    return E.reshape(G, B), P.reshape(G, B)
+
+
 def _torch_energy_function():
     import torch
 
