@@ -7,10 +7,10 @@
  *
  *     |beta, gamma> = prod_{k=1}^{p} e^{-i beta_k H_D} e^{-i gamma_k H_C} |+>^n,
  *
- * with the mixer H_D = sum_i X_i (Sec. II.C.2) and the diagonal Ising cost
+ * with the mixer H_D = sum_i X_i (Sec. III.A.2) and the diagonal Ising cost
  * H_C = sum_i h_i Z_i + sum_{i<j} J_ij Z_i Z_j (Eq. HC), and reads out
- * <H_C> and the ground-state ("success") probability (Sec. III.A.1 and the
- * success-probability definition of Sec. II.B.3).
+ * <H_C> and the ground-state ("success") probability (Sec. III.B.1 and the
+ * success-probability definition of Sec. III.A.3).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -31,7 +31,7 @@
  *    every call that returns host values synchronises that stream.
  *  - Costs are exact integers: the weights h_i, J_ij must be integer
  *    multiples of 2^-s for some s in 0..3 (half-integers arise in the exact-
- *    cover mapping, Sec. II.B.3).  Internally costs are int32 in units of
+ *    cover mapping, Sec. III.A.3).  Internally costs are int32 in units of
  *    2^-s; qs_cost_info reports s.  Other weights give QS_ENOTINT.
  *
  * Thread safety: distinct handles may be used from distinct host threads;

@@ -17,16 +17,16 @@
  *     amplitudes that differ in bit j (Eq. twocomponentupdates).
  *   - H_C = sum_i h_i Z_i + sum_{i<j} J_ij Z_i Z_j (Eq. HC), diagonal; with
  *     the textbook convention Z|0> = +|0>, i.e. s_i(z) = 1 - 2 bit_i(z).
- *   - H_D = sum_i X_i (Sec. II.C.2, the mixer below Eq. QAOA_state).
+ *   - H_D = sum_i X_i (Sec. III.A.2, the mixer below Eq. QAOA_state).
  *   - |beta,gamma> = prod_{k=1}^p e^{-i beta_k H_D} e^{-i gamma_k H_C} |+>^n
  *     (Eq. QAOA_state; Appendix A spells out the factor order: the phase of
  *     layer k acts before its mixer).  e^{-i gamma H_C} is applied as one
  *     z-rotation per field term and one ZZ phase per coupling, and
- *     e^{-i beta H_D} as one x-rotation per qubit (Sec. III.A.1, the
+ *     e^{-i beta H_D} as one x-rotation per qubit (Sec. III.B.1, the
  *     paragraph on how JUQCS-G computes the exponentials).
  *   - readout: E = <H_C> and the ground-state ("success") probability, the
- *     total weight on all basis states of minimal cost (Sec. III.A.1 and the
- *     success-probability definition in Sec. II.B.3).
+ *     total weight on all basis states of minimal cost (Sec. III.B.1 and the
+ *     success-probability definition in Sec. III.A.3).
  *
  * The adjoint (reverse-mode derivative of the readout with respect to the
  * 2p angles) is not in the paper.  Here it is the textbook gate-by-gate

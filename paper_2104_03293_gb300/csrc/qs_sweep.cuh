@@ -1,7 +1,7 @@
 #pragma once
 // Tiled HBM sweep kernel: one read + one write of the state (or of psi and
 // lambda) per launch, with the x-rotations of the tile's target bits
-// (Eq. twocomponentupdates applied to e^{-i beta X}, Sec. III.A.1), the
+// (Eq. twocomponentupdates applied to e^{-i beta X}, Sec. III.B.1), the
 // diagonal phase e^{-i gamma H_C} (Eq. HC, computed from the bit pattern, no
 // 2^n diagonal), the readout (<H_C>, ground probability, norm) and the adjoint
 // accumulations fused in.

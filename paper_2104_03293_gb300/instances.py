@@ -8,7 +8,7 @@ two sides are always fed identical instances.
 An instance is the problem Hamiltonian of Eq. (HC),
 ``H_C = sum_i h_i Z_i + sum_{i<j} J_ij Z_i Z_j``, stored as
 ``(n, h[n], edges[m, 2] with i < j, J[m])``.  The exact-cover instances of the
-paper (Sec. II.B.3) are not available, so seeded graphs of the shapes named
+paper (Sec. III.A.3) are not available, so seeded graphs of the shapes named
 for each workload stand in for them:
 
 * 3-regular MaxCut: J_ij = +1 on the edges of a random 3-regular graph,

@@ -385,7 +385,7 @@ class Batch:
 
 def grid_scan(h, edges, J, gammas, betas, stream=None, return_batch: bool = False):
     """p = 1 landscapes of one instance over a (gamma, beta) grid (the
-    energy and success-probability maps of Sec. 3.2.1, Fig. 4, scanned there
+    energy and success-probability maps of Sec. III.B.1, Fig. 4, scanned there
     on 64 x 64 points, beta in [0, pi), gamma in [0, 2 pi)): E and
     P_ground at every point of gammas x betas, from one batched evolve of
     len(gammas) * len(betas) copies of the instance (qs_batch_*), each copy

@@ -25,7 +25,7 @@ def config1_record():
     val, dg, db = oracle.adjoint(inst, g, b, 0)
     return {
         "source": "CPU oracle (complex128, gate by gate): Eq. (QAOA_state) with H_C of Eq. (HC), "
-                  "readout of Sec. III.A.1; 3-regular MaxCut stand-in for the paper's instances",
+                  "readout of Sec. III.B.1; 3-regular MaxCut stand-in for the paper's instances",
         "n": inst.n, "edges": inst.edges.tolist(), "J": inst.J.tolist(), "h": inst.h.tolist(),
         "gamma": g.tolist(), "beta": b.tolist(),
         "cmin": cmin, "cmax": cmax, "argmin": arg, "ground_count": cnt,

@@ -1,4 +1,4 @@
-"""p = 1 landscape scan (Sec. 3.2.1, Fig. 4) through the batched path,
+"""p = 1 landscape scan (Sec. III.B.1, Fig. 4) through the batched path,
 against the oracle at every grid point."""
 import numpy as np
 import pytest
