@@ -17,7 +17,9 @@ formulas that are plain algebra:
   negative beta;
 * the paper's second-order map, Eqs. (beta_k)-(gamma_k) verbatim;
 * the chain rule from (dgamma, dbeta) to (dtau, ds_k) for both maps;
-* a float64 Adam step (bias-corrected) used to drive oracle gradients.
+* a float64 Adam step (bias-corrected) used to drive oracle gradients;
+* the exact-cover objective of Eq. (exactcover) from its definition, over
+  all assignments (the pin of the exact-cover to Ising mapping).
 
 Every function works on the instance fields ``n, h, edges, J`` as produced by
 ``paper_2104_03293_gb300.instances`` (the shared seeded input generator).
@@ -119,6 +121,18 @@ def ground(inst):
     _load().orc_ground(inst.n, _ptr(h), e.shape[0], _ptr(e), _ptr(J),
                        _ptr(cmin), _ptr(cmax), _ptr(arg), _ptr(cnt))
     return float(cmin[0]), float(cmax[0]), int(arg[0]), int(cnt[0])
+
+
+def exact_cover_cost_all(a) -> np.ndarray:
+    """The exact-cover objective of Eq. (exactcover), sum over the F columns
+    of (sum_i a_if x_i - 1)^2, for every x in {0,1}^N (x_i = bit i of the
+    basis index), written out from its definition (int64)."""
+    a = np.asarray(a, dtype=np.int64)
+    N, F = a.shape
+    z = np.arange(1 << N, dtype=np.int64)
+    x = (z[:, None] >> np.arange(N, dtype=np.int64)[None, :]) & 1     # [2^N, N]
+    covered = x @ a                                                   # [2^N, F]
+    return ((covered - 1) ** 2).sum(axis=1)
 
 
 def plus_state(n: int) -> np.ndarray:

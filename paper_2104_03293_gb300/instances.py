@@ -17,6 +17,9 @@ for each workload stand in for them:
   uniformly from a symmetric range (optionally excluding J = 0).
 * Factorised instances: the union of independent components on disjoint,
   contiguous qubit ranges (the state is then a tensor product).
+* Exact-cover problem matrices with a planted solution (the problem class of
+  the paper, whose own instances are not available); the mapping to H_C is
+  part of the method and lives in the package, not here.
 
 Seeds follow ``seed = 2104032930 + 1000 * config + index``.
 """
@@ -120,6 +123,25 @@ def union(parts: Sequence[Instance], name: str = "") -> Instance:
         n += p.n
     return _canon(n, np.concatenate(h), edges, np.concatenate(J) if J else [],
                   name or "union_" + "_".join(p.name for p in parts), comps)
+
+
+def exact_cover(n: int, f: int, seed: int, extra_density: float | None = None):
+    """A random exact-cover problem matrix a in {0,1}^{n x f} (rows =
+    variables, columns = the f elements to cover) with a planted solution:
+    a random half of the variables (at least one) split the columns among
+    them, one owner per column; every other variable covers each column with
+    probability ``extra_density`` (default: the owners' mean density).
+    Returns (a as int8 [n, f], planted x as int8 [n])."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros(n, dtype=np.int8)
+    owners = rng.choice(n, size=max(1, n // 2), replace=False)
+    x[owners] = 1
+    a = np.zeros((n, f), dtype=np.int8)
+    a[rng.choice(owners, size=f), np.arange(f)] = 1
+    q = 1.0 / owners.size if extra_density is None else float(extra_density)
+    rest = np.flatnonzero(x == 0)
+    a[rest] = (rng.random((rest.size, f)) < q).astype(np.int8)
+    return a, x
 
 
 def uniform_angles(p: int, seed: int, lo: float = 0.0, hi: float = np.pi):
