@@ -97,3 +97,10 @@ def test_planner_matches_host_mirror(lib, dtype):
         for g, w in zip(got, want):
             if w["kind"] == 1:
                 assert (g["g0"], g["n1"], g["g1"]) == (w["g0"], w["n1"], w["g1"]), (n, g, w)
+
+
+def test_grid_scan_rejects_an_empty_grid_before_any_device_call(lib):
+    with pytest.raises(qs.QSError):
+        qs.grid_scan(np.zeros(3), np.zeros((0, 2), dtype=np.int32), np.zeros(0), [], [0.1])
+    with pytest.raises(qs.QSError):
+        qs.grid_scan(np.zeros(3), np.zeros((0, 2), dtype=np.int32), np.zeros(0), [0.2], np.zeros(0))
