@@ -131,6 +131,26 @@ def _stream_ptr(stream) -> Optional[int]:
     return getattr(stream, "cuda_stream", None) or None
 
 
+def _ising_arrays(n: int, h, edges, J):
+    """Contiguous (h, edges, J) for the C calls, with the lengths the C side
+    reads checked here: h has n entries and J one per edge."""
+    h = _f64(h)
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    J = _f64(J)
+    if h.ndim != 1 or h.size != n:
+        raise ValueError(f"h has {h.size} entries, expected {n}")
+    if J.ndim != 1 or J.size != e.shape[0]:
+        raise ValueError(f"J has {J.size} entries for {e.shape[0]} edges")
+    return h, e, J
+
+
+def _angles(gamma, beta):
+    g, b = _f64(gamma), _f64(beta)
+    if g.ndim != 1 or g.shape != b.shape:
+        raise ValueError("gamma and beta must be 1-D and of the same length")
+    return g, b
+
+
 def phys_qubits(n: int) -> int:
     return max(n, MIN_PHYS_QUBITS)
 
@@ -140,7 +160,12 @@ class State:
 
     def __init__(self, n: int, dtype: str = "c64", stream=None, buffer=None):
         self.n = int(n)
-        self.dtype = QS_C64 if dtype in ("c64", "complex64", QS_C64) else QS_C128
+        if dtype in ("c64", "complex64", QS_C64):
+            self.dtype = QS_C64
+        elif dtype in ("c128", "complex128", QS_C128):
+            self.dtype = QS_C128
+        else:
+            raise ValueError(f"dtype {dtype!r}: expected 'c64' or 'c128'")
         self.elem = 8 if self.dtype == QS_C64 else 16
         self._buffer = buffer  # keep a caller tensor alive
         self._adj = None
@@ -173,18 +198,14 @@ class State:
         _check(lib().qs_set_path(self._h, int(path)))
 
     def set_ising(self, h, edges, J):
-        h = _f64(h)
-        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
-        J = _f64(J)
+        h, e, J = _ising_arrays(self.n, h, edges, J)
         _check(lib().qs_set_ising(self._h, _dptr(h), int(e.shape[0]), e.ctypes.data_as(_PI32), _dptr(J)))
 
     def set_instance(self, inst):
         self.set_ising(inst.h, inst.edges, inst.J)
 
     def evolve(self, gamma, beta, from_plus: bool = True):
-        g, b = _f64(gamma), _f64(beta)
-        if g.shape != b.shape:
-            raise ValueError("gamma and beta differ in length")
+        g, b = _angles(gamma, beta)
         _check(lib().qs_evolve(self._h, int(g.size), _dptr(g), _dptr(b), int(bool(from_plus))))
 
     def readout(self):
@@ -225,7 +246,7 @@ class State:
         _check(lib().qs_set_adjoint_buffer(self._h, ptr, nbytes))
 
     def grad(self, gamma, beta, objective: int = QS_OBJ_ENERGY):
-        g, b = _f64(gamma), _f64(beta)
+        g, b = _angles(gamma, beta)
         dg, db = np.zeros_like(g), np.zeros_like(b)
         v = ctypes.c_double()
         _check(lib().qs_grad(self._h, int(g.size), _dptr(g), _dptr(b), int(objective), ctypes.byref(v), _dptr(dg),
@@ -254,9 +275,7 @@ class State:
 def enumerate_noalloc(h, edges, J, cuda_stream=None):
     """qs_enumerate_noalloc: (cmin, cmax, argmin, ground_count, shift) of the
     Ising cost, computed with the library's static device scratch."""
-    h = _f64(h)
-    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
-    J = _f64(J)
+    h, e, J = _ising_arrays(np.asarray(h).size, h, edges, J)
     vals = [ctypes.c_int64() for _ in range(4)]
     s = ctypes.c_int()
     _check(lib().qs_enumerate_noalloc(int(h.size), _dptr(h), int(e.shape[0]), e.ctypes.data_as(_PI32), _dptr(J),
@@ -342,20 +361,24 @@ class Batch:
             pass
 
     def set_ising(self, idx: int, h, edges, J):
-        h = _f64(h)
-        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
-        J = _f64(J)
+        if not 0 <= int(idx) < self.count:
+            raise ValueError(f"instance index {idx} out of range [0, {self.count})")
+        h, e, J = _ising_arrays(int(self.ns[int(idx)]), h, edges, J)
         _check(lib().qs_batch_set_ising(self._h, int(idx), _dptr(h), int(e.shape[0]), e.ctypes.data_as(_PI32),
                                         _dptr(J)))
 
-    def _layout(self, gammas):
+    def _layout(self, gammas, betas=None):
+        if len(gammas) != self.count or (betas is not None and len(betas) != self.count):
+            raise ValueError(f"expected one angle list per instance ({self.count})")
+        if betas is not None and any(len(g) != len(b) for g, b in zip(gammas, betas)):
+            raise ValueError("gamma and beta lists differ in length for some instance")
         p = np.ascontiguousarray(np.asarray([len(g) for g in gammas], dtype=np.int32))
         off = np.zeros(self.count, dtype=np.int64)
         off[1:] = np.cumsum(p[:-1])
         return p, off
 
     def evolve(self, gammas, betas):
-        p, off = self._layout(gammas)
+        p, off = self._layout(gammas, betas)
         g = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in gammas]) if p.sum() else np.zeros(1))
         b = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in betas]) if p.sum() else np.zeros(1))
         self.p, self.off = p, off
@@ -377,6 +400,11 @@ class Batch:
         return v, self._split(dg), self._split(db)
 
     def adam(self, gammas, betas, steps: int, lr=0.01, b1=0.9, b2=0.999, eps=1e-8, use_graph: bool = True):
+        if self.p is None:
+            raise QSError(QS_ESTATE, "Batch.adam: evolve the batch first (it fixes each instance's p)")
+        p, _ = self._layout(gammas, betas)
+        if not np.array_equal(p, self.p):
+            raise ValueError("Batch.adam: the angle lists must have the lengths of the last evolve")
         g = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in gammas]))
         b = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in betas]))
         _check(lib().qs_batch_adam(self._h, int(steps), lr, b1, b2, eps, _dptr(g), _dptr(b), int(bool(use_graph))))

@@ -104,3 +104,22 @@ def test_grid_scan_rejects_an_empty_grid_before_any_device_call(lib):
         qs.grid_scan(np.zeros(3), np.zeros((0, 2), dtype=np.int32), np.zeros(0), [], [0.1])
     with pytest.raises(qs.QSError):
         qs.grid_scan(np.zeros(3), np.zeros((0, 2), dtype=np.int32), np.zeros(0), [0.2], np.zeros(0))
+
+
+def test_binding_checks_the_lengths_the_c_side_reads(lib):
+    """The binding rejects arrays shorter than what the C entry points read
+    (h of n entries, one J per edge, matching angle lists) before calling."""
+    h, e, J = qs._ising_arrays(3, [0.5, 0, -1], [[0, 1], [1, 2]], [1.0, -1.0])
+    assert h.shape == (3,) and e.shape == (2, 2) and e.dtype == np.int32 and J.shape == (2,)
+    with pytest.raises(ValueError):
+        qs._ising_arrays(4, [0.5, 0, -1], [[0, 1]], [1.0])
+    with pytest.raises(ValueError):
+        qs._ising_arrays(3, [0.5, 0, -1], [[0, 1], [1, 2]], [1.0])
+    with pytest.raises(ValueError):
+        qs.enumerate_noalloc([0.0, 1.0], [[0, 1]], [])
+    with pytest.raises(ValueError):
+        qs._angles([0.1, 0.2], [0.3])
+    with pytest.raises(ValueError):
+        qs._angles([[0.1]], [[0.3]])
+    with pytest.raises(ValueError):
+        qs.State(4, dtype="c32")
