@@ -145,7 +145,7 @@ def _ising_arrays(n: int, h, edges, J):
 
 
 def _angles(gamma, beta):
-    g, b = _f64(gamma), _f64(beta)
+    g, b = _f64(np.atleast_1d(gamma)), _f64(np.atleast_1d(beta))  # a scalar is one layer
     if g.ndim != 1 or g.shape != b.shape:
         raise ValueError("gamma and beta must be 1-D and of the same length")
     return g, b

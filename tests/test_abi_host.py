@@ -121,5 +121,7 @@ def test_binding_checks_the_lengths_the_c_side_reads(lib):
         qs._angles([0.1, 0.2], [0.3])
     with pytest.raises(ValueError):
         qs._angles([[0.1]], [[0.3]])
+    g, b = qs._angles(0.1, 0.3)  # a scalar is one layer
+    assert g.shape == b.shape == (1,)
     with pytest.raises(ValueError):
         qs.State(4, dtype="c32")
