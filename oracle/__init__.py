@@ -17,6 +17,7 @@ formulas that are plain algebra:
   negative beta;
 * the paper's second-order map, Eqs. (beta_k)-(gamma_k) verbatim;
 * the chain rule from (dgamma, dbeta) to (dtau, ds_k) for both maps;
+* the per-layer spin expectations <Z_i> recorded during AQA (in ``oracle.c``);
 * a float64 Adam step (bias-corrected) used to drive oracle gradients;
 * the exact-cover objective of Eq. (exactcover) from its definition, over
   all assignments (the pin of the exact-cover to Ising mapping).
@@ -78,6 +79,9 @@ def _load():
         lib.orc_evolve.argtypes = [I, P, P, I, P, P, I, P, P, I]
         lib.orc_readout.argtypes = [I, P, P, I, P, P, D, P, P, P]
         lib.orc_adjoint.argtypes = [I, P, I, P, P, I, P, P, I, D, P, P, P, P, P]
+        lib.orc_zexp.argtypes = [I, P, P]
+        lib.orc_evolve_zexp.argtypes = [I, P, P, I, P, P, I, P, P, P]
+        lib.orc_set_threads.argtypes = [I]
         lib.orc_num_threads.restype = I
         _lib = lib
         return lib
@@ -97,6 +101,11 @@ def _fields(inst):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_threads(t: int) -> None:
+    """Number of host threads of the oracle's OpenMP loops (t >= 1)."""
+    _load().orc_set_threads(int(t))
 
 
 def cost(inst, z: int) -> float:
@@ -181,6 +190,28 @@ def readout(inst, psi, cmin=None):
     return float(E[0]), float(P[0]), float(nrm[0])
 
 
+def zexp(inst, psi) -> np.ndarray:
+    """<Z_i> = sum_z |psi_z|^2 s_i(z) for every qubit i of one state."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros(inst.n)
+    _load().orc_zexp(inst.n, _ptr(psi), _ptr(out))
+    return out
+
+
+def evolve_zexp(inst, gamma, beta) -> np.ndarray:
+    """<Z_i> after every layer of Eq. (QAOA_state) from |+>^n: array [p, n]
+    (the spin expectation values recorded during AQA, Sec. III.B.2, Fig. 6)."""
+    h, e, J = _fields(inst)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    assert g.shape == b.shape
+    psi = np.empty(1 << inst.n, dtype=np.complex128)
+    out = np.zeros((g.size, inst.n))
+    _load().orc_evolve_zexp(inst.n, _ptr(psi), _ptr(h), e.shape[0], _ptr(e), _ptr(J),
+                            g.size, _ptr(g), _ptr(b), _ptr(out))
+    return out
+
+
 def expect(inst, gamma, beta):
     """(E, P_ground) of |beta, gamma>."""
     E, P, _ = readout(inst, evolve(inst, gamma, beta))
@@ -238,6 +269,33 @@ def aqa_angles_second_order(tau: float, s) -> tuple:
     beta[:-1] = -tau * (A[1:] + A[:-1]) / 2.0
     beta[-1] = -tau * A[-1] / 2.0
     return tau * s, beta
+
+
+def aqa_chain_second_order(tau: float, s, dgamma, dbeta):
+    """(dF/dtau, dF/ds_k) for the map of ``aqa_angles_second_order``.
+
+    Written from that map term by term: gamma_k = tau s_k gives s_k dF/dgamma_k
+    to dtau and tau dF/dgamma_k to ds_k; beta_k = -tau (A(s_{k+1}) + A(s_k)) / 2
+    (k < p) and beta_p = -tau A(s_p) / 2 give beta_k / tau dF/dbeta_k to dtau
+    and, with dA/ds = -1, tau / 2 dF/dbeta_k to ds_k and to ds_{k+1}."""
+    s = np.asarray(s, dtype=np.float64)
+    dg = np.asarray(dgamma, dtype=np.float64)
+    db = np.asarray(dbeta, dtype=np.float64)
+    p = s.size
+    A = 1.0 - s
+    dtau = 0.0
+    ds = np.zeros(p)
+    for k in range(p):
+        dtau += s[k] * dg[k]
+        ds[k] += tau * dg[k]
+        if k + 1 < p:
+            dtau += -(A[k + 1] + A[k]) / 2.0 * db[k]
+            ds[k] += tau / 2.0 * db[k]
+            ds[k + 1] += tau / 2.0 * db[k]
+        else:
+            dtau += -A[k] / 2.0 * db[k]
+            ds[k] += tau / 2.0 * db[k]
+    return float(dtau), ds
 
 
 def adam_step(theta, grad, m, v, t, lr=0.01, b1=0.9, b2=0.999, eps=1e-8):

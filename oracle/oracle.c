@@ -248,6 +248,49 @@ void orc_adjoint(int n, const double* h, int m, const int32_t* edges, const doub
     }
 }
 
+/*
+ * Spin expectation values <Z_i> = sum_z |psi_z|^2 s_i(z), i = 0..n-1, of one
+ * state (the per-qubit <sigma^z_i> that the AQA runs record during the time
+ * evolution, Sec. III.B.2, shown in Fig. 6).  One plain pass per qubit.
+ */
+void orc_zexp(int n, const cplx* psi, double* out)
+{
+    uint64_t N = (uint64_t)1 << n;
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+        for (int64_t z = 0; z < (int64_t)N; ++z) {
+            double w = creal(psi[z]) * creal(psi[z]) + cimag(psi[z]) * cimag(psi[z]);
+            acc += w * spin((uint64_t)z, i);
+        }
+        out[i] = acc;
+    }
+}
+
+/* Eq. (QAOA_state) from |+>^n, recording <Z_i> after every layer:
+ * out[k * n + i] for layers k = 0..p-1 (after the mixer of layer k). */
+void orc_evolve_zexp(int n, cplx* psi, const double* h, int m, const int32_t* edges, const double* J,
+                     int p, const double* gamma, const double* beta, double* out)
+{
+    orc_init_plus(n, psi);
+    for (int k = 0; k < p; ++k) {
+        orc_layer(n, psi, h, m, edges, J, gamma[k], beta[k]);
+        orc_zexp(n, psi, out + (size_t)k * n);
+    }
+}
+
+/* Host threads used by the OpenMP loops above (timing of the CPU baseline
+ * with all cores and with one). */
+void orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -280,6 +280,71 @@ def test_second_order_map_is_a_product_of_symmetric_steps():
     assert np.linalg.norm(ref - phase * psi) <= 1e-12
 
 
+def test_second_order_chain_rule_matches_differences():
+    """dP/dtau and dP/ds_k under the second-order map (Eqs. beta_k-gamma_k,
+    Appendix A): the oracle's chain rule applied to its adjoint against
+    central differences of P_ground taken through the map itself."""
+    inst = I.erdos_renyi_ising(7, 52)
+    p, tau = 6, 0.8
+    s = np.arange(p) / (p - 1)
+
+    def F(t, ss):
+        g, b = oracle.aqa_angles_second_order(t, ss)
+        return oracle.expect(inst, g, b)[1]
+
+    g, b = oracle.aqa_angles_second_order(tau, s)
+    _, dg, db = oracle.adjoint(inst, g, b, 1)
+    dtau, ds = oracle.aqa_chain_second_order(tau, s, dg, db)
+    eps = 1e-6
+    assert abs(dtau - (F(tau + eps, s) - F(tau - eps, s)) / (2 * eps)) <= 1e-7
+    for k in range(p):
+        e = np.zeros(p); e[k] = eps
+        assert abs(ds[k] - (F(tau, s + e) - F(tau, s - e)) / (2 * eps)) <= 1e-7
+    # the first-order chain rule applied to the second-order angles is wrong
+    # (it misses the knot s_{k+1} inside beta_k): the pin can tell them apart
+    _, ds1 = oracle.aqa_chain(tau, s, dg, db)
+    assert np.max(np.abs(ds1 - ds)) > 1e-3
+
+
+# ---------------------------------------------------------------- spin expectations
+@pytest.mark.parametrize("idx", [1, 3, 4, 5])
+def test_zexp_matches_dense_pauli_expectations(idx):
+    """<Z_i> after every layer (Sec. III.B.2, Fig. 6) against
+    <psi_k| Z_i |psi_k> with Z_i the Kronecker product and psi_k from dense
+    matrix exponentials."""
+    inst = small_instances()[idx]
+    p = 3
+    g, b = I.uniform_angles(p, 300 + idx)
+    got = oracle.evolve_zexp(inst, g, b)
+    assert got.shape == (p, inst.n)
+    for k in range(p):
+        psi = dense_state(inst, g[:k + 1], b[:k + 1])
+        for i in range(inst.n):
+            ref = np.vdot(psi, pauli(inst.n, {i: PZ}) @ psi).real
+            assert abs(got[k, i] - ref) <= 1e-12
+
+
+def test_zexp_special_cases_and_closed_form():
+    inst = I.erdos_renyi_ising(9, 71)
+    # gamma = 0: the state stays |+> (an eigenvector of H_D); beta = 0: the
+    # phase leaves |psi|^2 uniform.  Either way every <Z_i> vanishes.
+    assert np.max(np.abs(oracle.evolve_zexp(inst, [0.0, 0.0], [0.3, 1.1]))) <= 1e-14
+    assert np.max(np.abs(oracle.evolve_zexp(inst, [0.4, 0.9], [0.0, 0.0]))) <= 1e-14
+    # fields only, one layer: each qubit evolves alone, e^{-i b X} e^{-i g h Z}|+>
+    # has <Z> = sin(2 b) sin(2 g h) (a 2 x 2 computation)
+    h = np.array([1.0, -2.0, 0.5, 0.0, 3.0])
+    fields = I._canon(5, h, [], [], "fields")
+    g, b = 0.37, 0.81
+    got = oracle.evolve_zexp(fields, [g], [b])[0]
+    assert np.max(np.abs(got - np.sin(2 * b) * np.sin(2 * g * h))) <= 1e-14
+    # and then E = sum_i h_i <Z_i> at every layer
+    g3, b3 = I.uniform_angles(3, 72)
+    z = oracle.evolve_zexp(fields, g3, b3)
+    for k in range(3):
+        E, _ = oracle.expect(fields, g3[:k + 1], b3[:k + 1])
+        assert abs(E - float(h @ z[k])) <= 1e-13
+
+
 # ---------------------------------------------------------------- Adam
 def test_adam_matches_torch():
     torch = pytest.importorskip("torch")
