@@ -36,7 +36,7 @@ def test_exact_cover_on_the_cuda_path(qs, n, f):
     E, P, N = st.readout()
     Er, Pr = oracle.expect(inst, np.asarray(g) / r, b)
     bound = float(np.abs(h).sum() + np.abs(J).sum())
-    assert abs(E - Er) <= 1e-5 * max(abs(Er), bound, 1.0) and abs(P - Pr) <= 1e-5 and abs(N - 1) <= 1e-5
+    assert abs(E - Er) <= 1e-5 * max(abs(Er), bound, 1.0) and abs(P - Pr) <= 1e-4 * Pr + 1e-9 and abs(N - 1) <= 1e-5
     if n <= 14:
         assert np.linalg.norm(st.copy_state() - oracle.evolve(inst, np.asarray(g) / r, b)) <= 1e-4
     st.close()

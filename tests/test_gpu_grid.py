@@ -27,11 +27,12 @@ def test_grid_scan_matches_oracle(qs):
         for c, b in enumerate(betas):
             Er, Pr = oracle.expect(inst, [g], [b])
             assert abs(E[a, c] - Er) <= 1e-5 * max(abs(Er), bound, 1.0), (a, c, E[a, c], Er)
-            assert abs(P[a, c] - Pr) <= 1e-5, (a, c, P[a, c], Pr)
+            assert abs(P[a, c] - Pr) <= 1e-4 * Pr + 1e-9, (a, c, P[a, c], Pr)
     # gamma = 0 or beta = 0 leaves |+>^n's statistics: E = sum h_i <Z_i> + ... = 0, P = count / 2^n
     cmin, cmax, arg, cnt = oracle.ground(inst)
     assert np.all(np.abs(E[0, :]) <= 1e-5 * max(bound, 1.0)) and np.all(np.abs(E[:, 0]) <= 1e-5 * max(bound, 1.0))
-    assert np.allclose(P[0, :], cnt / 2.0 ** inst.n, atol=1e-6) and np.allclose(P[:, 0], cnt / 2.0 ** inst.n, atol=1e-6)
+    P0 = cnt / 2.0 ** inst.n
+    assert np.allclose(P[0, :], P0, rtol=1e-4, atol=1e-9) and np.allclose(P[:, 0], P0, rtol=1e-4, atol=1e-9)
 
 
 def test_grid_scan_rejects_an_empty_grid(qs):

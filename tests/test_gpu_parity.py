@@ -1,10 +1,13 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI.
 
-Tolerances (from the stated targets): state ||psi - psi_ref||_2 <= 1e-4 for
-complex64 (1e-10 for complex128); readout |E - E_ref| <= 1e-5 max(|E_ref|,
-sum|h| + sum|J|) and |P - P_ref| <= 1e-5; ground-state data bit-exact.
-Sizes span several tiles, every tile shape, ragged last shapes and the
-padded small-n case.
+Tolerances (tests/tolerances.py): state ||psi - psi_ref||_2 <= 1e-4 for
+complex64 (1e-10 for complex128); |E - E_ref| <= 1e-5 max(|E_ref|, sum|h| +
+sum|J|); |P - P_ref| <= 1e-4 P_ref + 1e-9; gradients within 1e-4 of the
+largest reference component; ground-state data bit-exact.  Sizes span
+several tiles, every tile shape, ragged last shapes and the padded small-n
+case; AQA angles (first-order map, p = 10-20) give ground probabilities of
+0.2-0.8, so the P and dP comparisons bite; deep circuits (p = 100) bound the
+accumulated float32 rounding.
 """
 import json
 import os
@@ -14,6 +17,7 @@ import pytest
 
 import oracle
 from paper_2104_03293_gb300 import instances as I
+from tolerances import assert_grad, assert_readout, e_tol, p_tol, value_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +27,6 @@ def qs():
     from paper_2104_03293_gb300 import build, qs as _qs
     build.build()
     return _qs
-
-
-def e_tol(inst, E_ref):
-    return 1e-5 * max(abs(E_ref), float(np.abs(inst.h).sum() + np.abs(inst.J).sum()), 1.0)
 
 
 def run(qs, inst, g, b, dtype="c64", path=0):
@@ -47,11 +47,10 @@ def check_state(qs, inst, g, b, dtype="c64", path=0, tol=None):
     tol = tol if tol is not None else (1e-4 if dtype == "c64" else 1e-10)
     err = np.linalg.norm(psi - ref)
     assert err <= tol, (inst.name, err)
-    assert abs(E - Er) <= e_tol(inst, Er), (E, Er)
-    assert abs(P - Pr) <= 1e-5, (P, Pr)
+    assert_readout(inst, E, P, Er, Pr, inst.name)
     assert abs(N - 1.0) <= 1e-5
     st.close()
-    return err
+    return err, Pr
 
 
 def test_config1_golden(qs):
@@ -63,7 +62,7 @@ def test_config1_golden(qs):
         Pg, arg, cmin, cnt = st.ground_prob()
         assert (arg, cmin, cnt) == (rec["argmin"], rec["cmin"], rec["ground_count"])
         tol = 1e-12 if dtype == "c128" else e_tol(inst, rec["E"])
-        assert abs(E - rec["E"]) <= tol and abs(P - rec["P_ground"]) <= (1e-12 if dtype == "c128" else 1e-5)
+        assert abs(E - rec["E"]) <= tol and abs(P - rec["P_ground"]) <= (1e-12 if dtype == "c128" else p_tol(rec["P_ground"]))
     check_state(qs, inst, g, b, "c128")
     check_state(qs, inst, g, b, "c64")
 
@@ -113,7 +112,7 @@ def test_p0_and_continuation(qs):
     assert np.linalg.norm(st.copy_state() - ref) <= 1e-4
     E, P, _ = st.readout()
     Er, Pr, _ = oracle.readout(inst, ref)
-    assert abs(E - Er) <= e_tol(inst, Er) and abs(P - Pr) <= 1e-5
+    assert_readout(inst, E, P, Er, Pr)
 
 
 @pytest.mark.parametrize("n,seed", [(1, 1), (5, 2), (8, 3), (12, 4), (19, 5), (24, 6)])
@@ -151,10 +150,8 @@ def test_adjoint_matches_oracle(qs, objective, n, p):
     st.set_instance(inst)
     v, dg, db = st.grad(g, b, objective)
     vr, dgr, dbr = oracle.adjoint(inst, g, b, objective)
-    scale = max(1.0, float(np.max(np.abs(np.concatenate([dgr, dbr])))))
-    assert abs(v - vr) <= 1e-5 * max(1.0, abs(vr))
-    assert np.max(np.abs(dg - dgr)) <= 1e-4 * scale, (dg, dgr)
-    assert np.max(np.abs(db - dbr)) <= 1e-4 * scale, (db, dbr)
+    assert abs(v - vr) <= value_tol(objective, inst, vr), (v, vr)
+    assert_grad(np.concatenate([dg, db]), np.concatenate([dgr, dbr]), what=(n, p, objective))
 
 
 def test_batched_matches_single(qs):
@@ -169,4 +166,65 @@ def test_batched_matches_single(qs):
         Es, Ps, _ = st.readout()
         assert E[i] == Es and P[i] == Ps  # same kernels, same per-tile order
         Er, Pr = oracle.expect(inst, g, b)
-        assert abs(E[i] - Er) <= e_tol(inst, Er) and abs(P[i] - Pr) <= 1e-5
+        assert_readout(inst, E[i], P[i], Er, Pr, i)
+
+
+def _aqa(p, tau=0.75):
+    return oracle.aqa_angles(tau, np.arange(1, p + 1) / (p + 1))
+
+
+def _workload_instance(n, k):
+    """ER(4) Ising with h, J in U{-1,0,1}: the distribution of the n = 34 run."""
+    return I.erdos_renyi_ising(n, I.workload_seed(5, 300 + n + 1000 * k), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+
+
+@pytest.mark.parametrize("n", [12, 17, 21, 24])
+def test_state_parity_aqa_large_ground_probability(qs, n):
+    """First-order AQA (tau = 0.75, p = 20): the regime of the benchmark, where
+    the ground-state probability is large, so |P - P_ref| <= 1e-4 P_ref is a
+    sharp check of the readout.  n = 12 is padded, 17 and 21 take two and three
+    tile shapes, 24 the packed-pair strided sweeps."""
+    inst = _workload_instance(n, 0)
+    g, b = _aqa(20)
+    _, Pr = check_state(qs, inst, g, b)
+    assert Pr > 0.1, Pr
+
+
+@pytest.mark.parametrize("objective", [1, 0])
+@pytest.mark.parametrize("n,p", [(12, 10), (17, 12), (21, 10), (24, 10)])
+def test_adjoint_aqa_large_ground_probability(qs, objective, n, p):
+    """Gradients at AQA angles, where P_ground and its derivatives are large:
+    every component within 1e-4 of the largest reference component."""
+    inst = _workload_instance(n, 1)
+    g, b = _aqa(p)
+    st = qs.State(n)
+    st.set_instance(inst)
+    v, dg, db = st.grad(g, b, objective)
+    st.close()
+    vr, dgr, dbr = oracle.adjoint(inst, g, b, objective)
+    if objective == 1:
+        assert vr > 0.05, vr
+    assert abs(v - vr) <= value_tol(objective, inst, vr), (v, vr)
+    assert_grad(np.concatenate([dg, db]), np.concatenate([dgr, dbr]), what=(n, p, objective))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,p", [(20, 100), (24, 100)])
+def test_state_parity_deep_circuit(qs, n, p):
+    """p = 100 layers at uniform random angles: the accumulated float32
+    rounding of (n + 1) p tangent-form rotations and phases stays inside the
+    complex64 state tolerance."""
+    inst = I.erdos_renyi_ising(n, 6000 + n)
+    g, b = I.uniform_angles(p, 6100 + n)
+    err, _ = check_state(qs, inst, g, b)
+    assert err <= 1e-4
+
+
+@pytest.mark.slow
+def test_state_parity_n26_p20_aqa(qs):
+    """n = 26 (512 MiB complex64 state, three tile shapes), p = 20 AQA layers,
+    element by element against the oracle."""
+    inst = _workload_instance(26, 2)
+    g, b = _aqa(20)
+    _, Pr = check_state(qs, inst, g, b)
+    assert Pr > 0.05, Pr
