@@ -89,16 +89,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(n: int = 26, layers: int = 1, seed_cfg: int = 5, target_s: float = 0.0):
+def oracle_sample(n: int = 26, layers: int = 1, seed_cfg: int = 5, target_s: float = 0.0, threads: int = 0):
     """Time the CPU oracle on one seeded ER(4) instance of the workload family
     (h, J in U{-1,0,1}, AQA angles tau = 0.75): gate-by-gate complex128 layers
     at n qubits and the readout.  With target_s > 0 the layer count is chosen
     from a one-layer probe so the timed sample takes about target_s seconds.
+    threads > 0 sets the oracle's host threads (0: all cores).
     Returns (amplitude-updates/s, seconds, threads, layers)."""
     import numpy as np
     import oracle
     from paper_2104_03293_gb300 import instances as I
     inst = I.erdos_renyi_ising(n, I.workload_seed(seed_cfg, 0), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
 
     def run(L):
         s = np.arange(1, L + 1) / (L + 1)
@@ -113,6 +115,24 @@ def oracle_sample(n: int = 26, layers: int = 1, seed_cfg: int = 5, target_s: flo
         layers = max(1, min(64, int(round(target_s / max(t1, 1e-3)))))
     dt = run(layers)
     return layers * (n + 1) * 2.0 ** n / dt, dt, oracle.num_threads(), layers
+
+
+def cpu_baseline_table(n_main: int, n_bench: int):
+    """The oracle on the host cores at n = 20, 24 and n_main, with all cores
+    and with one (one AQA layer + readout each; the one-core run at n_main is
+    left out: about half a minute on its own).  The n_bench figure is a
+    per-amplitude extrapolation of the all-core n_main rate, labelled so."""
+    cores = os.cpu_count() or 1
+    rows = []
+    for n in (20, 24, n_main):
+        for thr in ((cores, 1) if n < n_main else (cores,)):
+            v, dt, used, L = oracle_sample(n, 1, threads=thr)
+            rows.append({"n": n, "threads": used, "layers": L, "seconds": round(dt, 3),
+                         "amplitude_updates_per_s": v})
+    main = [r for r in rows if r["n"] == n_main][0]
+    layer_s = (n_bench + 1) * 2.0 ** n_bench / main["amplitude_updates_per_s"]
+    return main, rows, {"n": n_bench, "layer_s": layer_s, "label": "extrapolated per amplitude from the "
+                        f"n={n_main} all-core rate (a complex128 n={n_bench} state needs {16 * 2 ** n_bench / 1e9:.0f} GB)"}
 
 
 def profiled_traffic():
@@ -408,10 +428,13 @@ def main():
     extra = None if args.no_secondary else secondary_workloads(qs, I, torch)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v_cpu, dt_cpu, thr, L = oracle_sample(args.ref_n, target_s=12.0)
-        cpu = {"value": v_cpu, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"{L} gate-by-gate complex128 AQA layers + readout at n={args.ref_n}, ER(4) "
-                         f"h,J in U{{-1,0,1}} ({dt_cpu:.1f} s); the n={n} state does not fit host memory"}
+        main_row, rows, extrap = cpu_baseline_table(args.ref_n, n)
+        cpu = {"value": main_row["amplitude_updates_per_s"], "unit": UNIT, "cores": main_row["threads"],
+               "kind": "oracle", "cores_available": os.cpu_count(),
+               "sample": f"one gate-by-gate complex128 AQA layer + readout at n={args.ref_n}, ER(4) h,J in "
+                         f"U{{-1,0,1}}, all {main_row['threads']} host threads ({main_row['seconds']} s); also "
+                         f"n=20 and 24 with all threads and with one (table)",
+               "table": rows, "n34_layer": extrap}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -252,6 +252,15 @@ int qs_aqa_angles_2nd(int p, double tau, const double* s, double* gamma, double*
 int qs_aqa_chain(int p, double tau, const double* s, const double* dgamma, const double* dbeta,
                  double* dtau, double* ds);
 
+/* Chain rule for qs_aqa_angles_2nd (Eqs. beta_k-gamma_k, Appendix A): from
+ * dF/dgamma_k, dF/dbeta_k to dF/dtau and dF/ds_k.  With A(s) = 1 - s,
+ *   dF/dtau = sum_k s_k dF/dgamma_k + sum_k (beta_k / tau) dF/dbeta_k,
+ *   dF/ds_k = tau dF/dgamma_k + tau/2 dF/dbeta_k + tau/2 dF/dbeta_{k-1} (k > 1),
+ * since beta_k holds A(s_k) and A(s_{k+1}) with weight tau/2 each (beta_p
+ * only A(s_p)).  p >= 1 knots; ds receives p values.  Errors: QS_EINVAL. */
+int qs_aqa_chain_2nd(int p, double tau, const double* s, const double* dgamma, const double* dbeta,
+                     double* dtau, double* ds);
+
 /* Thread-local text for the last non-OK status on this thread. */
 const char* qs_last_error(void);
 
@@ -299,6 +308,22 @@ int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2,
                   double* gamma_io, double* beta_io, int use_graph);
 
 int qs_batch_destroy(qs_batch_handle b);
+
+/* Partition of a batch over `world` ranks (one GPU each), host only.
+ * Instances are independent (no data-path exchange), so the only choice is
+ * which rank evolves which: greedy longest-first bin-packing on the work of
+ * an instance, max(p_i, 1) 2^{n_i} amplitude-layers (its HBM traffic is
+ * proportional to it).  Instances are taken in order of decreasing work
+ * (ties: lower index first), each to the rank with the least work so far
+ * (ties: lower rank).  Deterministic, so every rank computes the same
+ * partition from the same inputs.
+ *   count   instances; n, p: count ints each (n in 1..QS_MAX_QUBITS_C64,
+ *           p >= 0).
+ *   world   ranks, >= 1.
+ *   rank_of count ints: the rank of each instance.
+ *   load    world doubles (may be NULL): the work given to each rank.
+ * Errors: QS_EINVAL. */
+int qs_batch_partition(int count, const int* n, const int* p, int world, int* rank_of, double* load);
 
 #define QS_MAX_LAYERS_BATCH 64
 

@@ -212,6 +212,7 @@ struct qs_state {
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
     int grid[2][5] = {};  // [adjoint][kernel kind; 3, 4 = packed-pair kernel, phase / lean]
+    bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
     int device = 0;
     ShapeRule rule;                      // tile-shape plan (qs_set_shape_rule / qs_autotune)
     std::vector<double> ising_h, ising_J;  // the last qs_set_ising input, to re-plan
@@ -220,6 +221,9 @@ struct qs_state {
 
 static int check_handle(qs_handle h) {
     if (!h) return set_error(QS_EINVAL, "NULL handle");
+    if (h->poisoned)
+        return set_error(QS_ESTATE, "the handle is unusable after a tile copy outlived its kernel; destroy it and "
+                                    "create a new one");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
     return QS_OK;
@@ -242,6 +246,14 @@ static int check_device_error(qs_handle h) {
     if (v) {
         cudaMemset(h->err.ptr, 0, sizeof(int));
         h->have_readout = false;
+        if (v >= 2) {
+            // the exit drain gave up too: a copy may have landed in shared
+            // memory after its kernel ended, so nothing on this handle (or
+            // computed after that kernel) can be trusted
+            h->poisoned = true;
+            return set_error(QS_ETIMEOUT, "a sweep kernel gave up waiting for a tile copy and for its drain; the "
+                                          "state and later results are invalid and the handle is unusable");
+        }
         return set_error(QS_ETIMEOUT, "a sweep kernel gave up waiting for a tile copy; the state is invalid");
     }
     return QS_OK;
@@ -825,6 +837,27 @@ int qs_aqa_chain(int p, double tau, const double* s, const double* dgamma, const
     for (int k = 0; k < p; ++k) {
         t += s[k] * dgamma[k] - (1.0 - s[k]) * dbeta[k];
         ds[k] = tau * (dgamma[k] + dbeta[k]);
+    }
+    *dtau = t;
+    return QS_OK;
+}
+
+int qs_aqa_chain_2nd(int p, double tau, const double* s, const double* dgamma, const double* dbeta, double* dtau,
+                     double* ds) {
+    if (p < 1 || !s || !dgamma || !dbeta || !ds || !dtau || !std::isfinite(tau))
+        return set_error(QS_EINVAL, "qs_aqa_chain_2nd: bad arguments");
+    double t = 0;
+    for (int k = 0; k < p; ++k) ds[k] = tau * dgamma[k];
+    for (int k = 0; k < p; ++k) {
+        t += s[k] * dgamma[k];
+        const double A = 1.0 - s[k];
+        if (k + 1 < p) {
+            t -= 0.5 * ((1.0 - s[k + 1]) + A) * dbeta[k];
+            ds[k + 1] += 0.5 * tau * dbeta[k];
+        } else {
+            t -= 0.5 * A * dbeta[k];
+        }
+        ds[k] += 0.5 * tau * dbeta[k];
     }
     *dtau = t;
     return QS_OK;

@@ -70,6 +70,7 @@ struct qs_batch {
     int grid[2][3] = {};  // [adjoint][kernel kind]
     cudaGraphExec_t graph = nullptr;
     bool have_results = false;
+    bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
     int objective = 0;
 };
 
@@ -87,7 +88,20 @@ static int batch_check_err(qs_batch_handle b) {
     if (!v) return QS_OK;
     cudaMemset(b->err.ptr, 0, sizeof(int));
     b->have_results = false;
+    if (v >= 2) {
+        b->poisoned = true;
+        return set_error(QS_ETIMEOUT, "a sweep kernel gave up waiting for a tile copy and for its drain; results "
+                                      "are invalid and the batch is unusable");
+    }
     return set_error(QS_ETIMEOUT, "a sweep kernel gave up waiting for a tile copy; results are invalid");
+}
+
+static int check_batch(qs_batch_handle b) {
+    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (b->poisoned)
+        return set_error(QS_ESTATE, "the batch is unusable after a tile copy outlived its kernel; destroy it and "
+                                    "create a new one");
+    return QS_OK;
 }
 
 static void drop_graph(qs_batch_handle b) {
@@ -128,7 +142,7 @@ int qs_batch_create(qs_batch_handle* out, int count, const int* n, int dtype, vo
 
 int qs_batch_set_ising(qs_batch_handle b, int idx, const double* hfield, int n_edges, const int32_t* edges,
                        const double* J) {
-    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (int rc = check_batch(b)) return rc;
     if (idx < 0 || idx >= b->count) return set_error(QS_EINVAL, "qs_batch_set_ising: idx %d out of range", idx);
     cudaSetDevice(b->device);
     Instance tmp;
@@ -373,7 +387,7 @@ extern "C" {
 
 int qs_batch_evolve(qs_batch_handle b, const int* p, const int64_t* angle_off, const double* gamma,
                     const double* beta) {
-    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (int rc = check_batch(b)) return rc;
     if (!p || !angle_off || !gamma || !beta) return set_error(QS_EINVAL, "qs_batch_evolve: NULL argument");
     cudaSetDevice(b->device);
     for (int i = 0; i < b->count; ++i) {
@@ -410,7 +424,7 @@ int qs_batch_evolve(qs_batch_handle b, const int* p, const int64_t* angle_off, c
 }
 
 int qs_batch_results(qs_batch_handle b, double* E, double* P) {
-    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (int rc = check_batch(b)) return rc;
     if (!b->have_results) return set_error(QS_ESTATE, "qs_batch_results: nothing evolved yet");
     cudaSetDevice(b->device);
     std::vector<double> r(3 * (size_t)b->count);
@@ -426,7 +440,7 @@ int qs_batch_results(qs_batch_handle b, double* E, double* P) {
 }
 
 int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamma, double* dbeta) {
-    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (int rc = check_batch(b)) return rc;
     if ((int)b->p.size() != b->count) return set_error(QS_ESTATE, "qs_batch_grad: call qs_batch_evolve first");
     if (objective != QS_OBJ_ENERGY && objective != QS_OBJ_GROUND) return set_error(QS_EINVAL, "bad objective");
     if (b->total > 0 && (!dgamma || !dbeta)) return set_error(QS_EINVAL, "dgamma or dbeta is NULL");
@@ -454,7 +468,7 @@ int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamm
 
 int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2, double eps, double* gamma_io,
                   double* beta_io, int use_graph) {
-    if (!b) return set_error(QS_EINVAL, "NULL batch");
+    if (int rc = check_batch(b)) return rc;
     if ((int)b->p.size() != b->count) return set_error(QS_ESTATE, "qs_batch_adam: call qs_batch_evolve first");
     if (steps < 0 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) || !(eps > 0))
         return set_error(QS_EINVAL, "qs_batch_adam: bad hyper-parameters");
@@ -538,6 +552,31 @@ int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2,
         }
     b->host_angles = a;
     b->have_results = true;
+    return QS_OK;
+}
+
+int qs_batch_partition(int count, const int* n, const int* p, int world, int* rank_of, double* load) {
+    if (count < 0 || world < 1 || (count > 0 && (!n || !p || !rank_of)))
+        return set_error(QS_EINVAL, "qs_batch_partition: bad arguments");
+    std::vector<double> work(count);
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || n[i] > QS_MAX_QUBITS_C64 || p[i] < 0)
+            return set_error(QS_EINVAL, "qs_batch_partition: instance %d has n = %d, p = %d", i, n[i], p[i]);
+        work[i] = std::ldexp((double)std::max(p[i], 1), n[i]);
+    }
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> acc(world, 0.0);
+    for (int i : order) {
+        int r = 0;
+        for (int q = 1; q < world; ++q)
+            if (acc[q] < acc[r]) r = q;
+        rank_of[i] = r;
+        acc[r] += work[i];
+    }
+    if (load)
+        for (int q = 0; q < world; ++q) load[q] = acc[q];
     return QS_OK;
 }
 

@@ -678,8 +678,10 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         }
     }
     // On a timeout, wait (bounded) for a copy still in flight before the CTA's
-    // shared memory goes away.
-    if (tid == 0 && pending) mbar_wait_bounded(full, parity);
+    // shared memory goes away; if that wait also gives up, a copy may still
+    // land in shared memory the SM hands to a later CTA: report it with the
+    // sticky status 2 (the host then refuses to use the handle again).
+    if (tid == 0 && pending && !mbar_wait_bounded(full, parity)) atomicMax(err, 2);
 }
 
 template <class Real, int K, int R, int NA, int KIND, int V>

@@ -337,10 +337,11 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             }
         }
     }
-    // before the shared memory goes away: wait (bounded) for copies in flight
+    // before the shared memory goes away: wait (bounded) for copies in flight;
+    // a drain that gives up is reported with the sticky status 2
     if (tid == 0)
         for (int q = 0; q < NB; ++q)
-            if ((pend >> q) & 1u) mbar_wait_bounded(full + q, (phase >> q) & 1u);
+            if (((pend >> q) & 1u) && !mbar_wait_bounded(full + q, (phase >> q) & 1u)) atomicMax(err, 2);
     __syncthreads();
 }
 

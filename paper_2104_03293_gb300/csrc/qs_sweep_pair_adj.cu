@@ -391,7 +391,8 @@ __global__ void __launch_bounds__(256, 1)
             __syncthreads();
         }
     }
-    if (tid == 0 && pending) mbar_wait_bounded(full, parity);
+    // a drain that gives up is reported with the sticky status 2
+    if (tid == 0 && pending && !mbar_wait_bounded(full, parity)) atomicMax(err, 2);
 }
 
 template <int C>

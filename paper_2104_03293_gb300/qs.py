@@ -67,6 +67,7 @@ _SIGS = {
     "qs_aqa_angles": [_I, _D, _PD, _PD, _PD],
     "qs_aqa_angles_2nd": [_I, _D, _PD, _PD, _PD],
     "qs_aqa_chain": [_I, _D, _PD, _PD, _PD, _PD, _PD],
+    "qs_aqa_chain_2nd": [_I, _D, _PD, _PD, _PD, _PD, _PD],
     "qs_launch_count": [_PI64],
     "qs_plan_shape": [_I, _I, _I, _PI, _PI, _PI, _PI, _PI, _PI],
     "qs_last_error": [],
@@ -78,6 +79,7 @@ _SIGS = {
     "qs_batch_grad": [_P, _I, _PD, _PD, _PD],
     "qs_batch_adam": [_P, _I, _D, _D, _D, _D, _PD, _PD, _I],
     "qs_batch_destroy": [_P],
+    "qs_batch_partition": [_I, _PI, _PI, _I, _PI, _PD],
 }
 
 
@@ -325,6 +327,16 @@ def aqa_chain(tau: float, s, dgamma, dbeta):
     return dt.value, ds
 
 
+def aqa_chain_2nd(tau: float, s, dgamma, dbeta):
+    """(dF/dtau, dF/ds_k) under the second-order map of aqa_angles_2nd."""
+    s, dg, db = _f64(s), _f64(dgamma), _f64(dbeta)
+    ds = np.zeros_like(s)
+    dt = ctypes.c_double()
+    _check(lib().qs_aqa_chain_2nd(int(s.size), float(tau), _dptr(s), _dptr(dg), _dptr(db), ctypes.byref(dt),
+                                  _dptr(ds)))
+    return dt.value, ds
+
+
 def version() -> str:
     return lib().qs_version().decode()
 
@@ -393,6 +405,8 @@ class Batch:
         return [flat[o:o + k].copy() for o, k in zip(self.off, self.p)]
 
     def grad(self, objective: int = QS_OBJ_ENERGY):
+        if self.p is None:
+            raise QSError(QS_ESTATE, "Batch.grad: evolve the batch first (it fixes each instance's angles)")
         tot = int(self.p.sum())
         v = np.zeros(self.count)
         dg, db = np.zeros(max(tot, 1)), np.zeros(max(tot, 1))
@@ -409,6 +423,20 @@ class Batch:
         b = _f64(np.concatenate([np.asarray(x, dtype=np.float64) for x in betas]))
         _check(lib().qs_batch_adam(self._h, int(steps), lr, b1, b2, eps, _dptr(g), _dptr(b), int(bool(use_graph))))
         return self._split(g), self._split(b)
+
+
+def batch_partition(ns, ps, world: int):
+    """qs_batch_partition: (rank of each instance, work per rank), the
+    greedy longest-first bin-packing of max(p, 1) 2^n over `world` ranks."""
+    n = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+    p = np.ascontiguousarray(np.asarray(ps, dtype=np.int32))
+    if n.shape != p.shape or n.ndim != 1:
+        raise ValueError("ns and ps must be 1-D and of the same length")
+    rank_of = np.zeros(n.size, dtype=np.int32)
+    load = np.zeros(max(int(world), 1))
+    _check(lib().qs_batch_partition(int(n.size), n.ctypes.data_as(_PI), p.ctypes.data_as(_PI), int(world),
+                                    rank_of.ctypes.data_as(_PI), _dptr(load)))
+    return rank_of, load
 
 
 def grid_scan(h, edges, J, gammas, betas, stream=None, return_batch: bool = False):
@@ -472,27 +500,32 @@ def _torch_aqa_function():
     import torch
 
     class QSAqa(torch.autograd.Function):
-        """F(tau, s) of the first-order AQA angles (qs_aqa_angles); backward
-        uses qs_grad and the chain rule of qs_aqa_chain."""
+        """F(tau, s) of the AQA angles (order 1: qs_aqa_angles, order 2:
+        qs_aqa_angles_2nd); backward uses qs_grad and the matching chain rule
+        (qs_aqa_chain or qs_aqa_chain_2nd)."""
 
         @staticmethod
-        def forward(ctx, tau, s, state, objective=QS_OBJ_ENERGY):
+        def forward(ctx, tau, s, state, objective=QS_OBJ_ENERGY, order=1):
             t = float(tau.detach().cpu().double())
             sk = s.detach().cpu().double().numpy()
-            g, b = aqa_angles(t, sk)
+            g, b = aqa_angles(t, sk) if order == 1 else aqa_angles_2nd(t, sk)
             val, dg, db = state.grad(g, b, objective)
-            dt, ds = aqa_chain(t, sk, dg, db)
+            dt, ds = aqa_chain(t, sk, dg, db) if order == 1 else aqa_chain_2nd(t, sk, dg, db)
             ctx.save_for_backward(torch.tensor(dt, dtype=tau.dtype), torch.from_numpy(ds).to(s.dtype))
             return torch.tensor(val, dtype=tau.dtype)
 
         @staticmethod
         def backward(ctx, grad_out):
             dt, ds = ctx.saved_tensors
-            return grad_out * dt, grad_out * ds, None, None
+            return grad_out * dt, grad_out * ds, None, None, None
 
     return QSAqa
 
 
-def aqa_energy(tau, s, state: State, objective: int = QS_OBJ_ENERGY):
-    """Differentiable AQA objective in (tau, schedule knots s_k) through torch.autograd."""
-    return _torch_aqa_function().apply(tau, s, state, objective)
+def aqa_energy(tau, s, state: State, objective: int = QS_OBJ_ENERGY, order: int = 1):
+    """Differentiable AQA objective in (tau, schedule knots s_k) through
+    torch.autograd, for the first-order map (order 1) or the paper's
+    second-order map of Appendix A (order 2)."""
+    if order not in (1, 2):
+        raise ValueError("order must be 1 or 2")
+    return _torch_aqa_function().apply(tau, s, state, objective, order)

@@ -63,6 +63,21 @@ def test_aqa_angles_match_oracle(lib, p):
         assert abs(dt - dto) <= 1e-12 and np.allclose(ds, dso, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("p", [1, 2, 7, 20])
+def test_aqa_chain_2nd_matches_oracle(lib, p):
+    """The library's chain rule for the second-order map against the
+    oracle's term-by-term restatement (pinned by finite differences)."""
+    rng = np.random.default_rng(100 + p)
+    s = np.sort(rng.uniform(0, 1, size=p))
+    for tau in (0.4, 0.8):
+        dg, db = rng.normal(size=p), rng.normal(size=p)
+        dt, ds = qs.aqa_chain_2nd(tau, s, dg, db)
+        dto, dso = oracle.aqa_chain_second_order(tau, s, dg, db)
+        assert abs(dt - dto) <= 1e-12 and np.allclose(ds, dso, rtol=0, atol=1e-12)
+    with pytest.raises(qs.QSError):
+        qs.aqa_chain_2nd(0.5, [], [], [])
+
+
 def test_aqa_bad_arguments(lib):
     with pytest.raises(qs.QSError):
         qs.aqa_angles(float("nan"), [0.5])
