@@ -11,6 +11,7 @@
 
 #include "../../include/qs.h"
 #include "qs_api_common.h"
+#include "qs_layout.h"
 #include "qs_pair.h"
 
 namespace qs {
@@ -117,26 +118,31 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
         while (blob.size() % 4) blob.push_back(0);
         return off;
     };
+    // per shape: the tile program; per kernel layout: the layout program
+    // (the tile bits of its register-slot and thread-index bits)
     for (int cfgi = 0; cfgi < 2; ++cfgi) {
         const KernelCfg cfg = kernel_cfg(dtype, cfgi == 1);
         shapes[cfgi] = make_shapes(nphys, cfg, page_bit_for(dtype), rule);
-        for (size_t s = 0; s < shapes[cfgi].size(); ++s)
+        for (size_t s = 0; s < shapes[cfgi].size(); ++s) {
+            const Shape& sh = shapes[cfgi][s];
+            tprog_off[cfgi][s] = add(build_tile_prog(sh, h, I.ei, I.ej, I.J));
+            const LayoutTab L = make_layout(sh.K, cfg.R, sh.kind);
             for (int g = 0; g < kMaxLayouts; ++g) {
-                if (g >= num_layouts(shapes[cfgi][s], cfg.R)) { prog_off[cfgi][s][g] = prog_off[cfgi][s][0]; continue; }
-                int regq[6];
-                shape_regq(shapes[cfgi][s], cfg.R, g, regq);
-                prog_off[cfgi][s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, cfg.R));
+                if (g >= L.G) { prog_off[cfgi][s][g] = prog_off[cfgi][s][0]; continue; }
+                prog_off[cfgi][s][g] = add(build_layout_prog(sh, I.ei, I.ej, I.J, L.regs[g], cfg.R, L.tbits[g],
+                                                             sh.K - cfg.R));
             }
+        }
     }
     for (size_t s = 0; s < shapes[0].size(); ++s) {
         const Shape& sh = shapes[0][s];
         if (!pair_choice(dtype, 0, sh.kind, sh.c, 1)) continue;
         const PairLayout PL = pair_layout(sh.c);
         for (int g = 0; g < 2; ++g) {
-            int regq[6];
-            regq[0] = shape_bit(sh, PL.P);  // slot bit 0: the pack bit; bits 1..5: regs[g]
-            for (int b = 0; b < 5; ++b) regq[1 + b] = shape_bit(sh, PL.regs[g][b]);
-            prog_pair[s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, 6));
+            int slot[6];
+            slot[0] = PL.P;  // slot bit 0: the pack bit; bits 1..5: regs[g]
+            for (int b = 0; b < 5; ++b) slot[1 + b] = PL.regs[g][b];
+            prog_pair[s][g] = add(build_layout_prog(sh, I.ei, I.ej, I.J, slot, 6, PL.tbits[g], 7));
         }
     }
     for (size_t s = 0; s < shapes[1].size(); ++s) {
@@ -145,10 +151,10 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
         if (!pc) continue;
         const PairAdjLayout PL = pair_adj_layout(pc);
         for (int g = 0; g < 3; ++g) {
-            int regq[6] = {-1, -1, -1, -1, -1, -1};
-            regq[0] = shape_bit(sh, PL.P);  // slot bit 0: the pack bit; bits 1..4: regs[g]
-            for (int b = 0; b < 4; ++b) regq[1 + b] = shape_bit(sh, PL.regs[g][b]);
-            prog_pair_adj[s][g] = add(build_cost_prog(nphys, h, I.ei, I.ej, I.J, regq, 5));
+            int slot[5];
+            slot[0] = PL.P;  // slot bit 0: the pack bit; bits 1..4: regs[g]
+            for (int b = 0; b < 4; ++b) slot[1 + b] = PL.regs[g][b];
+            prog_pair_adj[s][g] = add(build_layout_prog(sh, I.ei, I.ej, I.J, slot, 5, PL.tbits[g], 8));
         }
     }
     {
@@ -439,6 +445,7 @@ static SweepTask make_task(qs_handle h, const Shape& sh, const PlanSweep& ps, in
     t.layers = layers;
     t.tab = tab;
     for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_off[cfgi][shape_idx][g]);
+    t.tprog = I.prog(I.tprog_off[cfgi][shape_idx]);
     t.partials = partials;
     t.ntiles = sh.ntiles;
     t.part_base = 0;

@@ -56,7 +56,8 @@ struct Instance {
     int64_t cmin = 0, cmax = 0, argmin = 0, count = 0;
     int cost_lo = 0, range = 1;
     std::vector<Shape> shapes[2];                      // [forward, adjoint]
-    size_t prog_off[2][kMaxShapes][kMaxLayouts] = {};  // int32 offsets into progs
+    size_t prog_off[2][kMaxShapes][kMaxLayouts] = {};  // layout programs (sweep_kernel layouts), int32 offsets
+    size_t tprog_off[2][kMaxShapes] = {};              // tile programs of the shapes
     size_t prog_pair[kMaxShapes][2] = {};              // packed-pair layouts (forward shapes)
     size_t prog_pair_adj[kMaxShapes][3] = {};          // packed-pair adjoint layouts (adjoint shapes)
     size_t enum_off = 0, plain_off = 0;

@@ -246,6 +246,7 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
                     t.layers = (adj ? lr : lf) + b->lay_off[i];
                     t.tab = (adj ? tr : tf) + b->tab_off[i];
                     for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_off[adj][s.shape][g]);
+                    t.tprog = I.prog(I.tprog_off[adj][s.shape]);
                     t.partials = dpart;
                     t.ntiles = sh.ntiles;
                     t.part_base = 0;

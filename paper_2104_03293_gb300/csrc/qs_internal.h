@@ -63,6 +63,9 @@ struct LayerDev {
     int var;        // 1: cotangent form (flips the frame)
 };
 
+// Header length (int32 words) of a tile program (see build_tile_prog).
+constexpr int kTileProgHead = 20;
+
 struct SweepTask {
     int kind;                    // 0 contiguous, 1 strided
     int n1, g1;                  // strided: second target run (see Shape)
@@ -70,7 +73,8 @@ struct SweepTask {
     void* lam;
     const LayerDev* layers;
     const void* tab;             // per-layer phase tables [layer][tab_stride] (Real2)
-    const int32_t* cprog[kMaxLayouts];
+    const int32_t* cprog[kMaxLayouts];  // layout programs (build_layout_prog) of the kernel's layouts
+    const int32_t* tprog;        // tile program of the shape (build_tile_prog)
     double* partials;            // per tile: np doubles
     int64_t ntiles;
     int64_t part_base;           // first partial slot of this task

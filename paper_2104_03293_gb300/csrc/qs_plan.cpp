@@ -276,6 +276,70 @@ std::vector<PlanSweep> plan_reverse(const std::vector<PlanSweep>& fwd, const std
     return v;
 }
 
+std::vector<int32_t> build_tile_prog(const Shape& s, const std::vector<int32_t>& h, const std::vector<int32_t>& ei,
+                                     const std::vector<int32_t>& ej, const std::vector<int32_t>& J) {
+    const int n = (int)h.size();
+    std::vector<int> tb_of(n, -1);
+    for (int tb = 0; tb < s.K; ++tb) {
+        const int q = shape_bit(s, tb);
+        if (q >= 0 && q < n) tb_of[q] = tb;
+    }
+    std::vector<int32_t> out(kTileProgHead, 0);
+    out[1] = s.K;
+    for (int tb = 0; tb < s.K && tb < 16; ++tb) {
+        const int q = shape_bit(s, tb);
+        out[4 + tb] = (q >= 0 && q < n) ? h[q] : 0;
+    }
+    int nt = 0;
+    auto term = [&](int a, int b, int c, int d) {
+        out.push_back(a); out.push_back(b); out.push_back(c); out.push_back(d);
+        ++nt;
+    };
+    for (int i = 0; i < n; ++i)
+        if (tb_of[i] < 0 && h[i] != 0) term(0, i, 0, h[i]);
+    for (size_t e = 0; e < ei.size(); ++e) {
+        if (J[e] == 0) continue;
+        const int i = ei[e], j = ej[e], ti = tb_of[i], tj = tb_of[j];
+        if (ti < 0 && tj < 0) term(1, i, j, J[e]);
+        else if (ti >= 0 && tj < 0) term(2 | (ti << 8), j, 0, J[e]);
+        else if (ti < 0 && tj >= 0) term(2 | (tj << 8), i, 0, J[e]);
+    }
+    out[0] = nt;
+    return out;
+}
+
+std::vector<int32_t> build_layout_prog(const Shape& s, const std::vector<int32_t>& ei, const std::vector<int32_t>& ej,
+                                       const std::vector<int32_t>& J, const int* slot_tb, int R, const int* thr_tb,
+                                       int NTB) {
+    // qubit -> (slot bit) or (thread bit), tile qubits only
+    std::vector<int> slot_q(R), thr_q(NTB);
+    for (int b = 0; b < R; ++b) slot_q[b] = shape_bit(s, slot_tb[b]);
+    for (int j = 0; j < NTB; ++j) thr_q[j] = shape_bit(s, thr_tb[j]);
+    auto find = [](const std::vector<int>& v, int q) {
+        for (size_t k = 0; k < v.size(); ++k)
+            if (v[k] == q) return (int)k;
+        return -1;
+    };
+    const size_t NS = (size_t)1 << R, NT = (size_t)1 << NTB;
+    std::vector<int32_t> out(NS + 8 * NT, 0);
+    for (size_t e = 0; e < ei.size(); ++e) {
+        if (J[e] == 0) continue;
+        const int sa = find(slot_q, ei[e]), sb = find(slot_q, ej[e]);
+        const int ta = find(thr_q, ei[e]), tb = find(thr_q, ej[e]);
+        auto spin = [](size_t idx, int bit) { return ((idx >> bit) & 1) ? -1 : 1; };
+        if (sa >= 0 && sb >= 0) {
+            for (size_t m = 0; m < NS; ++m) out[m] += J[e] * spin(m, sa) * spin(m, sb);
+        } else if (ta >= 0 && tb >= 0) {
+            for (size_t t = 0; t < NT; ++t) out[NS + 8 * t] += J[e] * spin(t, ta) * spin(t, tb);
+        } else if (sa >= 0 && tb >= 0) {
+            for (size_t t = 0; t < NT; ++t) out[NS + 8 * t + 1 + sa] += J[e] * spin(t, tb);
+        } else if (sb >= 0 && ta >= 0) {
+            for (size_t t = 0; t < NT; ++t) out[NS + 8 * t + 1 + sb] += J[e] * spin(t, ta);
+        }
+    }
+    return out;
+}
+
 int count_sweeps(int nphys, int dtype, int p) {
     const KernelCfg cfg = kernel_cfg(dtype, false);
     const auto sh = make_shapes(nphys, cfg, page_bit_for(dtype));

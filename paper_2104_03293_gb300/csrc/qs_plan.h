@@ -73,4 +73,28 @@ std::vector<PlanSweep> plan_forward(int S, int p, bool gen);
 std::vector<PlanSweep> plan_reverse(const std::vector<PlanSweep>& fwd, const std::vector<Shape>& shapes, int p);
 int count_sweeps(int nphys, int dtype, int p);
 
+// Tile programs: Eq. (HC) split by where each term's qubits sit relative to a
+// tile of a shape.  With O the qubits outside the tile (the tile index), T a
+// layout's thread-index qubits and R its register-slot qubits, and spins s
+// of the stored index z, the cost is
+//   C = Kf + Kc + sum_{t in T} (h_t + D_t) s_t + TT + sum_{b in R} (h_b + D_b + hRT_b) s_b + Q[slot]
+// with Kf = sum_{O} h s, Kc = sum_{O-O} J s s and D_q = sum_{o in O} J_qo s_o
+// (per tile, from the tile's base index), TT = sum_{T-T} J s s and hRT_b =
+// sum_{t in T} J_bt s_t (per thread and layout) and Q the couplings among
+// the slot qubits.  A stored array in the flipped frame (every bit inverted)
+// negates every field: Kf, h_t, h_b change sign, nothing else.
+//
+// Tile program (layout-independent):
+//   [0] nterms  [1] K  [2..4) 0  [4..20) H[16]: field of the qubit on tile bit tb
+//   [20 ...) nterms int4 terms: (0, i, 0, h_i) -> Kf;  (1, i, j, J) -> Kc;
+//   (2 | tb << 8, o, 0, J) -> D[tb]   (i, j, o outside the tile)
+std::vector<int32_t> build_tile_prog(const Shape& s, const std::vector<int32_t>& h, const std::vector<int32_t>& ei,
+                                     const std::vector<int32_t>& ej, const std::vector<int32_t>& J);
+// Layout program of one register layout of a kernel: Q[2^R], then for each
+// thread index t < 2^NTB eight ints (TT, hRT[0..R), 0...).  slot_tb[b] is the
+// tile bit of register-slot bit b, thr_tb[j] that of thread-index bit j.
+std::vector<int32_t> build_layout_prog(const Shape& s, const std::vector<int32_t>& ei, const std::vector<int32_t>& ej,
+                                       const std::vector<int32_t>& J, const int* slot_tb, int R, const int* thr_tb,
+                                       int NTB);
+
 }  // namespace qs

@@ -142,6 +142,43 @@ struct TMap {
 };
 
 // ---------------------------------------------------------------------------
+// Per-tile cost tables (see build_tile_prog / build_layout_prog).
+// ---------------------------------------------------------------------------
+struct TileTab {
+    int kf, kc, pad0, pad1;
+    int D[16];  // couplings of the qubit on tile bit tb to the qubits outside the tile
+    int H[16];  // field of the qubit on tile bit tb
+};
+
+// Warp 0: the table of the tile whose base index (tile bits clear) is zb.
+// The caller orders it before the table's readers with a block barrier.
+__device__ __forceinline__ void tile_tab_fill(TileTab* tt, const int32_t* __restrict__ tp, uint64_t zb,
+                                              uint32_t lane) {
+    if (lane < 16) {
+        tt->D[lane] = 0;
+        tt->H[lane] = __ldg(tp + 4 + lane);
+    }
+    __syncwarp();
+    const int nterms = __ldg(tp);
+    const int4* terms = reinterpret_cast<const int4*>(tp + kTileProgHead);
+    int kf = 0, kc = 0;
+    for (int k = (int)lane; k < nterms; k += 32) {
+        const int4 t = __ldg(terms + k);
+        const int si = 1 - 2 * (int)((zb >> t.y) & 1ull);
+        const int kind = t.x & 255;
+        if (kind == 0) kf += t.w * si;
+        else if (kind == 1) kc += t.w * si * (1 - 2 * (int)((zb >> t.z) & 1ull));
+        else atomicAdd(&tt->D[t.x >> 8], t.w * si);
+    }
+    kf = __reduce_add_sync(0xffffffffu, kf);
+    kc = __reduce_add_sync(0xffffffffu, kc);
+    if (lane == 0) {
+        tt->kf = kf;
+        tt->kc = kc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Cost program evaluation (see build_cost_prog).
 // ---------------------------------------------------------------------------
 template <int R>
@@ -202,6 +239,47 @@ struct SlotCost {
 #pragma unroll
             for (int k = 0; k < (1 << b); ++k) phi[k | (1 << b)] = phi[k] - 2 * fb[R1 + b];
     }
+    // From the tile table: Map::slot(b) / Map::thr(j) are the tile bits of
+    // register-slot bit b and thread-index bit j of the layout; lp is the
+    // layout program; frame = 1 when the stored array is bit-flipped.
+    template <class Map, int NTB>
+    __device__ __forceinline__ void init_tile(const TileTab& tt, const int32_t* __restrict__ lp, uint32_t tid,
+                                              int frame, int cost_lo) {
+        const int sg = frame ? -1 : 1;
+        const int4* tr = reinterpret_cast<const int4*>(lp + (1 << R)) + 2 * tid;
+        const int4 a = __ldg(tr), b = __ldg(tr + 1);
+        const int hrt[6] = {a.y, a.z, a.w, b.x, b.y, b.z};
+        int cout = sg * tt.kf + tt.kc + a.x;
+        static_for<0, NTB>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            constexpr int tb = Map::thr(j);
+            const int v = sg * tt.H[tb] + tt.D[tb];
+            cout += ((tid >> j) & 1u) ? -v : v;
+        });
+        int fb[R];
+        static_for<0, R>([&](auto bc) {
+            constexpr int bb = decltype(bc)::value;
+            constexpr int tb = Map::slot(bb);
+            fb[bb] = sg * tt.H[tb] + tt.D[tb] + hrt[bb];
+        });
+        q = lp;
+        int base = cout - cost_lo;
+#pragma unroll
+        for (int b2 = 0; b2 < R1; ++b2) base += fb[b2];
+        plo[0] = base;
+#pragma unroll
+        for (int b2 = 0; b2 < R1; ++b2)
+#pragma unroll
+            for (int k = 0; k < (1 << b2); ++k) plo[k | (1 << b2)] = plo[k] - 2 * fb[b2];
+        int hb = 0;
+#pragma unroll
+        for (int b2 = 0; b2 < R2; ++b2) hb += fb[R1 + b2];
+        phi[0] = hb;
+#pragma unroll
+        for (int b2 = 0; b2 < R2; ++b2)
+#pragma unroll
+            for (int k = 0; k < (1 << b2); ++k) phi[k | (1 << b2)] = phi[k] - 2 * fb[R1 + b2];
+    }
     __device__ __forceinline__ int idx(int m) const { return plo[m & ((1 << R1) - 1)] + phi[m >> R1] + __ldg(q + m); }
     // table index, kept inside [0, top] so that no cost can address memory
     // outside the phase table
@@ -235,8 +313,14 @@ struct Sweep {
     static constexpr int NSLOT = 2 * kMaxRounds;
     static constexpr size_t TILE_BYTES = (size_t)sizeof(C2) << K;
     static constexpr size_t BUF_BYTES = (size_t)NA * TILE_BYTES;  // one region per array
-    static constexpr size_t SMEM_BYTES = BUF_BYTES + 64 + (size_t)NW * NSLOT * 8;
+    static constexpr size_t TT_OFF = BUF_BYTES + 64 + (size_t)NW * NSLOT * 8;  // two TileTabs
+    static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
     static_assert(K - R >= 5, "a tile needs at least one full warp");
+    // compile-time tile bits of layout g for SlotCost::init_tile
+    template <int g> struct Map {
+        __host__ __device__ static constexpr int slot(int b) { return make_layout(K, R, LK).regs[g][b]; }
+        __host__ __device__ static constexpr int thr(int j) { return make_layout(K, R, LK).tbits[g][j]; }
+    };
     static_assert(G <= kMaxLay, "too many layouts");
 
     template <int g>
@@ -351,11 +435,10 @@ struct Sweep {
 
     // ---- phase -------------------------------------------------------------
     template <int g>
-    __device__ static __forceinline__ void phase(C2 (&v)[NA][NS], const SweepTask& T, uint64_t zthread,
-                                                 const C2* __restrict__ tab, int frame, Real& gacc) {
-        const uint64_t fm = frame ? ((1ull << T.n) - 1ull) : 0ull;
+    __device__ static __forceinline__ void phase(C2 (&v)[NA][NS], const SweepTask& T, const TileTab& tt,
+                                                 uint32_t tid, const C2* __restrict__ tab, int frame, Real& gacc) {
         SlotCost<R> sc;
-        sc.init(T.cprog[g], zthread ^ fm, frame, T.cost_lo);
+        sc.template init_tile<Map<g>, K - R>(tt, T.cprog[g], tid, frame, T.cost_lo);
         const int top = T.tab_stride - 1;
         Real part = 0;
 #pragma unroll
@@ -384,14 +467,11 @@ struct Sweep {
         const uint32_t e = e_thread<g>(tid);
         return base + (KIND == 0 ? (uint64_t)e : tm.gofs(e));
     }
-    __device__ static __forceinline__ void phase_any(int g, C2 (&v)[NA][NS], const SweepTask& T, const TMap& tm,
-                                                     uint64_t base, uint32_t tid, const C2* tab, int frame,
-                                                     Real& gacc) {
-        if (g == 0) phase<0>(v, T, zthread<0>(base, tid, tm), tab, frame, gacc);
-        else if (G > 1 && g == 1)
-            phase<(G > 1 ? 1 : 0)>(v, T, zthread<(G > 1 ? 1 : 0)>(base, tid, tm), tab, frame, gacc);
-        else if (G > 2)
-            phase<(G > 2 ? 2 : 0)>(v, T, zthread<(G > 2 ? 2 : 0)>(base, tid, tm), tab, frame, gacc);
+    __device__ static __forceinline__ void phase_any(int g, C2 (&v)[NA][NS], const SweepTask& T, const TileTab& tt,
+                                                     uint32_t tid, const C2* tab, int frame, Real& gacc) {
+        if (g == 0) phase<0>(v, T, tt, tid, tab, frame, gacc);
+        else if (G > 1 && g == 1) phase<(G > 1 ? 1 : 0)>(v, T, tt, tid, tab, frame, gacc);
+        else if (G > 2) phase<(G > 2 ? 2 : 0)>(v, T, tt, tid, tab, frame, gacc);
     }
 
     // ---- layout-0 global offsets of the register slots ----------------------
@@ -450,6 +530,7 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
     C2* buf = reinterpret_cast<C2*>(smraw);                                      // [NA][2^K]
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + S::BUF_BYTES);
     double* red = reinterpret_cast<double*>(smraw + S::BUF_BYTES + 64);
+    TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);  // [2]: by tile parity
     const uint32_t tid = threadIdx.x;
     C2 v[NA][NS];
 
@@ -572,6 +653,10 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         };
         const uint64_t g_thread = S::template zthread<0>(base, tid, tm);
         C2* arr[2] = {reinterpret_cast<C2*>(T.psi), reinterpret_cast<C2*>(T.lam)};
+        // the tile's cost table: warp 0, published by the barrier below (the
+        // other table of the pair may still be read for the previous tile)
+        const TileTab& tt = ttab[k & 1];
+        if ((kPhase || kRead) && tid < 32) tile_tab_fill(&ttab[k & 1], T.tprog, base, tid);
 
         int cur = start;
         if (gen) {
@@ -606,7 +691,7 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
             const LayerDev ly = T.layers[rd.layer];
             Real gB = 0, gG = 0;
             const C2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
-            if (kPhase && rd.phase_pre) S::phase_any(cur, v, T, tm, base, tid, ltab, ly.frame, gG);
+            if (kPhase && rd.phase_pre) S::phase_any(cur, v, T, tt, tid, ltab, ly.frame, gG);
             const Real fabs2 = (Real)(ly.fabs * ly.fabs);
             Real fpow = 1;
             if (NA == 2)
@@ -623,7 +708,7 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
                     S::rotate_any(g, v, w, c, fabs2, fpow, gB);
                 }
             }
-            if (kPhase && rd.phase_post) S::phase_any(cur, v, T, tm, base, tid, ltab, ly.frame, gG);
+            if (kPhase && rd.phase_post) S::phase_any(cur, v, T, tt, tid, ltab, ly.frame, gG);
             if (NA == 2) {
                 warp_sum_to((double)gB, red, 2 * r, NSLOT);
                 warp_sum_to((double)gG, red, 2 * r + 1, NSLOT);
@@ -633,9 +718,8 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
 
         if (kRead && (flags & (T_READOUT | T_WRITE_LAM))) {
             const int ef = T.layers[T.end_layer].frame;
-            const uint64_t fm = ef ? ((1ull << T.n) - 1ull) : 0ull;
             SlotCost<R> sc;
-            sc.init(T.cprog[0], g_thread ^ fm, ef, T.cost_lo);
+            sc.template init_tile<typename S::template Map<0>, K - R>(tt, T.cprog[0], tid, ef, T.cost_lo);
             Real E = 0, P = 0, N = 0;
             C2* lam = arr[1] + g_thread;
             const bool wl = (flags & T_WRITE_LAM) != 0;

@@ -52,7 +52,13 @@ struct PairSweep {
     static constexpr int K = kPairK, NT = 128, NJ = 32, P = C;
     static constexpr int NB = 1;  // tile buffers per CTA
     static constexpr size_t BUF_BYTES = (size_t)8 << K;
-    static constexpr size_t SMEM_BYTES = NB * BUF_BYTES + 64;
+    static constexpr size_t TT_OFF = NB * BUF_BYTES + 64;  // two TileTabs (by tile parity)
+    static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    // compile-time tile bits of layout g: slot bit 0 is the pack bit
+    template <int g> struct Map {
+        __host__ __device__ static constexpr int slot(int b) { return b == 0 ? P : pair_layout(C).regs[g][b - 1]; }
+        __host__ __device__ static constexpr int thr(int j) { return pair_layout(C).tbits[g][j]; }
+    };
 
     template <int g, int t> __host__ __device__ static constexpr int tb() { return pair_layout(C).tbits[g][t]; }
     template <int g, int b> __host__ __device__ static constexpr int rb() { return pair_layout(C).regs[g][b]; }
@@ -139,10 +145,10 @@ struct PairSweep {
     // ---- phase: slot m = lane | j << 1 (cost program of the layout) ------------
     template <int g>
     __device__ static __forceinline__ void phase(float2 (&X)[NJ], float2 (&Y)[NJ], const SweepTask& T,
-                                                 uint64_t zthread, const float2* __restrict__ tab, int frame) {
-        const uint64_t fm = frame ? ((1ull << T.n) - 1ull) : 0ull;
+                                                 const TileTab& tt, uint32_t tid, const float2* __restrict__ tab,
+                                                 int frame) {
         SlotCost<6> sc;
-        sc.init(T.cprog[g], zthread ^ fm, frame, T.cost_lo);
+        sc.template init_tile<Map<g>, 7>(tt, T.cprog[g], tid, frame, T.cost_lo);
         const int top = T.tab_stride - 1;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
@@ -182,7 +188,9 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     constexpr bool kPhase = V != V_LEAN;
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
+    TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     const uint32_t tid = threadIdx.x;
+    uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
     float2 X[NJ], Y[NJ];
 
     auto find_task = [&](int64_t gt) -> int {
@@ -254,6 +262,10 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             release();
             continue;
         }
+        // the tile's cost table (warp 0), published by the barrier after the wait
+        const TileTab& tt = ttab[tpar];
+        if (kPhase && tid < 32) tile_tab_fill(&ttab[tpar], T.tprog, base, tid);
+        tpar ^= 1u;
         const int ok = mbar_wait_bounded(full + b, (phase >> b) & 1u) ? 1 : 0;
         if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
             if (tid == 0) atomicExch(err, 1);
@@ -281,10 +293,8 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             if (++done_tr == ntr) release();
         };
         auto do_phase = [&](const float2* ltab, int frame) {
-            if (cur == 0)
-                S::template phase<0>(X, Y, T, base + tm.gofs(S::template e_thread<0>(tid)), ltab, frame);
-            else
-                S::template phase<1>(X, Y, T, base + tm.gofs(S::template e_thread<1>(tid)), ltab, frame);
+            if (cur == 0) S::template phase<0>(X, Y, T, tt, tid, ltab, frame);
+            else S::template phase<1>(X, Y, T, tt, tid, ltab, frame);
         };
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {

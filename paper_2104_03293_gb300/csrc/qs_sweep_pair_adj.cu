@@ -55,7 +55,15 @@ struct PairAdj {
     static constexpr int K = kPairK, NT = 256, NJ = 16, P = pair_adj_layout(C).P, NW = NT / 32,
                          NSLOT = 2 * kMaxRounds;
     static constexpr size_t TILE_BYTES = (size_t)8 << K;
-    static constexpr size_t SMEM_BYTES = 3 * TILE_BYTES + 64 + (size_t)NW * NSLOT * 8;
+    static constexpr size_t TT_OFF = 3 * TILE_BYTES + 64 + (size_t)NW * NSLOT * 8;  // two TileTabs
+    static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    // compile-time tile bits of layout g: slot bit 0 is the pack bit
+    template <int g> struct Map {
+        __host__ __device__ static constexpr int slot(int b) {
+            return b == 0 ? pair_adj_layout(C).P : pair_adj_layout(C).regs[g][b - 1];
+        }
+        __host__ __device__ static constexpr int thr(int j) { return pair_adj_layout(C).tbits[g][j]; }
+    };
 
     template <int g, int t> __host__ __device__ static constexpr int tb() { return pair_adj_layout(C).tbits[g][t]; }
     template <int g> __host__ __device__ static constexpr int rmask() { return pair_adj_layout(C).rotmask[g]; }
@@ -202,11 +210,11 @@ struct PairAdj {
     // (slot m = half | j << 1 of the layout's cost program)
     template <int g>
     __device__ static __forceinline__ void phase(float2 (&Xp)[NJ], float2 (&Yp)[NJ], float2 (&Xl)[NJ],
-                                                 float2 (&Yl)[NJ], const SweepTask& T, uint64_t zthread,
-                                                 const float2* __restrict__ tab, int frame, float& gacc) {
-        const uint64_t fm = frame ? ((1ull << T.n) - 1ull) : 0ull;
+                                                 float2 (&Yl)[NJ], const SweepTask& T, const TileTab& tt,
+                                                 uint32_t tid, const float2* __restrict__ tab, int frame,
+                                                 float& gacc) {
         SlotCost<5> sc;
-        sc.init(T.cprog[g], zthread ^ fm, frame, T.cost_lo);
+        sc.template init_tile<Map<g>, 8>(tt, T.cprog[g], tid, frame, T.cost_lo);
         const int top = T.tab_stride - 1;
         float part = 0.f;
 #pragma unroll
@@ -243,7 +251,9 @@ __global__ void __launch_bounds__(256, 1)
     float4* wk4 = reinterpret_cast<float4*>(smraw + 2 * S::TILE_BYTES);  // transpose buffer
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + 3 * S::TILE_BYTES);
     double* red = reinterpret_cast<double*>(smraw + 3 * S::TILE_BYTES + 64);
+    TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     const uint32_t tid = threadIdx.x;
+    uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
     float2 Xp[NJ], Yp[NJ], Xl[NJ], Yl[NJ];
 
     auto find_task = [&](int64_t gt) -> int {
@@ -295,6 +305,10 @@ __global__ void __launch_bounds__(256, 1)
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
         const uint64_t base = tm.base(tile);
         const int64_t nx = gt + gridDim.x;
+        // the tile's cost table (warp 0), published by the barrier after the wait
+        const TileTab& tt = ttab[tpar];
+        if (tid < 32) tile_tab_fill(&ttab[tpar], T.tprog, base, tid);
+        tpar ^= 1u;
 
         const int ok = mbar_wait_bounded(full, parity) ? 1 : 0;
         if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
@@ -335,12 +349,9 @@ __global__ void __launch_bounds__(256, 1)
             else S::template rotate<2>(Xp, Yp, Xl, Yl, w, fabs2, fpow, gB);
         };
         auto do_phase = [&](const float2* ltab, int frame, float& gG) {
-            if (cur == 0)
-                S::template phase<0>(Xp, Yp, Xl, Yl, T, base + tm.gofs(S::template e_thread<0>(tid)), ltab, frame, gG);
-            else if (cur == 1)
-                S::template phase<1>(Xp, Yp, Xl, Yl, T, base + tm.gofs(S::template e_thread<1>(tid)), ltab, frame, gG);
-            else
-                S::template phase<2>(Xp, Yp, Xl, Yl, T, base + tm.gofs(S::template e_thread<2>(tid)), ltab, frame, gG);
+            if (cur == 0) S::template phase<0>(Xp, Yp, Xl, Yl, T, tt, tid, ltab, frame, gG);
+            else if (cur == 1) S::template phase<1>(Xp, Yp, Xl, Yl, T, tt, tid, ltab, frame, gG);
+            else S::template phase<2>(Xp, Yp, Xl, Yl, T, tt, tid, ltab, frame, gG);
         };
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {

@@ -154,13 +154,15 @@ def test_config2_full_batch_against_oracle(qs):
         inst, g, b = items[i]
         Er, Pr = oracle.expect(inst, g, b)
         assert_readout(inst, E[i], P[i], Er, Pr, i)
+    # one at a time (single states use the packed-pair sweeps from 24 qubits,
+    # the batch the scalar ones: equal up to float32 rounding order)
     for i in range(0, 512, 37):
         inst, g, b = items[i]
         with qs.State(inst.n) as st:
             st.set_instance(inst)
             st.evolve(g, b)
             Es, Ps, _ = st.readout()
-        assert E[i] == Es and P[i] == Ps, i
+        assert_readout(inst, E[i], P[i], Es, Ps, i)
 
 
 @pytest.mark.slow
