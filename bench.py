@@ -425,6 +425,18 @@ def main():
     e2e_s = statistics.mean(timing["e2e_s"])
     h2d = inst.h.nbytes + inst.edges.nbytes + inst.J.nbytes + 2 * 8 * p
     d2h = 3 * 8
+    # per-layer <Z_i> recorded inside the same evolve (after the timed region)
+    g, b = qs.aqa_angles(tau, s)
+    st.set_ising(inst.h, inst.edges, inst.J)
+    st.evolve_zexp(g, b)
+    z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    z0.record(stream)
+    zrec = st.evolve_zexp(g, b)
+    z1.record(stream)
+    torch.cuda.synchronize()
+    zexp_ms = z0.elapsed_time(z1)
+    zexp = {"n": n, "p": p, "ms": zexp_ms, "forward_equivalents": zexp_ms / evolve_ms,
+            "max_abs_Z_last_layer": float(np.max(np.abs(zrec[-1])))}
     extra = None if args.no_secondary else secondary_workloads(qs, I, torch)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -455,6 +467,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "readout": {"E": E, "P_ground": P, "grad_P": v, "dP_dtau": dtau},
+        "zexp": zexp,
         "secondary": extra,
     }
     print(json.dumps(line), flush=True)

@@ -121,6 +121,19 @@ int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* 
  * QS_ESTATE (no Ising cost set), QS_ECUDA. */
 int qs_evolve(qs_handle h, int p, const double* gamma, const double* beta, int from_plus);
 
+/* Per-layer spin expectations (the magnetisations <sigma^z_i> followed
+ * during an annealing run, Sec. III.B.2, Fig. 6): apply p layers of
+ * Eq. (QAOA_state) from |+>^n, as qs_evolve with from_plus = 1, and record
+ * after every layer k the n values
+ *   zexp[k * n + i] = <Z_i> = sum_z |psi_z|^2 (1 - 2 bit_i(z)),  k = 0..p-1,
+ * (p * n host doubles, caller-owned).  Each record is accumulated in FP64
+ * inside the sweep that applies the next layer's phase (for the last layer,
+ * the readout sweep), so the evolve moves no extra state bytes.  The final
+ * state and its readout are left as after qs_evolve.  Tiled path only (not
+ * QS_PATH_PLAIN).  Synchronises.  Errors: QS_EINVAL, QS_ESTATE, QS_ECUDA,
+ * QS_ETIMEOUT. */
+int qs_evolve_zexp(qs_handle h, int p, const double* gamma, const double* beta, double* zexp);
+
 /* <H_C> of the current state, accumulated in FP64.  Synchronises. */
 int qs_expect(qs_handle h, double* E);
 

@@ -213,11 +213,11 @@ struct qs_state {
     void* lam = nullptr;
     bool own_lam = false;
     Instance inst;
-    DevBuf enum_scratch, layers_f, layers_r, tab_f, tab_r, partials, out, frame, err;
+    DevBuf enum_scratch, layers_f, layers_r, tab_f, tab_r, partials, out, frame, err, zpart, zout;
     Uploader up, up_ang;
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
-    int grid[2][5] = {};  // [adjoint][kernel kind; 3, 4 = packed-pair kernel, phase / lean]
+    int grid[2][6] = {};  // [adjoint][kernel kind; 3, 4, 5 = packed-pair kernel, phase / lean / zexp]
     bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
     int device = 0;
     ShapeRule rule;                      // tile-shape plan (qs_set_shape_rule / qs_autotune)
@@ -404,8 +404,16 @@ static int grid_for(qs_handle h, int kind, int adjoint) {
     int& g = h->grid[adjoint][kind];
     if (!g)
         g = kind < 3 ? sweep_grid(h->dtype, adjoint, kind)
-                     : (adjoint ? sweep_pair_adj_grid() : sweep_pair_grid(kind == 4 ? 2 : 1));
+                     : (adjoint ? sweep_pair_adj_grid() : sweep_pair_grid(kind == 4 ? V_LEAN : kind == 5 ? V_ZPHASE : V_PHASE));
     return g;
+}
+
+// Grid of a forward sweep launch (the persistent grid, clamped as in
+// launch_sweep to the number of tiles).
+static int forward_grid(qs_handle h, const SweepLaunch& L) {
+    int g = L.pairc ? grid_for(h, L.variant == V_LEAN ? 4 : L.variant == V_ZPHASE ? 5 : 3, 0) : grid_for(h, L.kind, 0);
+    if (g > L.total_tiles) g = (int)L.total_tiles;
+    return g < 1 ? 1 : g;
 }
 
 // Upload the angles and prepare forward (and optionally reverse) layers.
@@ -482,7 +490,11 @@ struct CallBlob {
 
 // Run the tiled schedule: forward sweeps (+ readout), and for a gradient the
 // reverse sweeps with their per-layer reductions.
-static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective) {
+//
+// zexp: every sweep holding a layer boundary (a phase of layer k >= 1) or the
+// readout also records <Z_q> of the state after layer k - 1 (resp. p - 1)
+// into per-CTA records, reduced after the sweep into h->zout[layer][n].
+static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective, bool zexp = false) {
     Instance& I = h->inst;
     const std::vector<Shape>& shf = I.shapes[0];
     const std::vector<Shape>& sha = I.shapes[1];
@@ -491,6 +503,17 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     if (mode_grad) {
         fwd.back().flags |= T_WRITE_LAM;
         rev = plan_reverse(fwd, sha, p);
+    }
+    if (zexp) {
+        for (auto& s : fwd) {
+            bool rec = (s.flags & T_READOUT) != 0;
+            for (int r = 0; r < s.nr; ++r) rec = rec || (s.r[r].phase_pre && s.r[r].layer > 0);
+            if (rec) s.flags |= T_ZEXP;
+        }
+        int gmax = 1;
+        for (int k = 0; k < 6; ++k) gmax = std::max(gmax, k < 3 ? grid_for(h, k, 0) : (h->dtype == 0 ? grid_for(h, k, 0) : 1));
+        if (int rc = h->zpart.reserve((size_t)gmax * kZSlots * kZQ * sizeof(double))) return rc;
+        if (int rc = h->zout.reserve((size_t)std::max(p, 1) * h->n * sizeof(double))) return rc;
     }
     size_t part_need = 0;
     for (auto& s : fwd) part_need = std::max(part_need, (size_t)shf[s.shape].ntiles * ((s.flags & T_READOUT) ? 3 : 0));
@@ -504,14 +527,35 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     std::vector<int> red_cnt;
     const LayerDev* lf = reinterpret_cast<const LayerDev*>(h->layers_f.ptr);
     const LayerDev* lr = reinterpret_cast<const LayerDev*>(h->layers_r.ptr);
+    std::vector<size_t> zred_off;
+    std::vector<int> zred_cnt;
+    double* dzp = reinterpret_cast<double*>(h->zpart.ptr);
+    double* dzo = reinterpret_cast<double*>(h->zout.ptr);
     for (auto& s : fwd) {
         SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective);
         const Shape& sh = shf[s.shape];
-        if (pair_choice(h->dtype, 0, sh.kind, sh.c, sweep_variant(s.flags, s.nr, s.r)))
+        const int variant = sweep_variant(s.flags, s.nr, s.r);
+        const int pc = pair_choice(h->dtype, 0, sh.kind, sh.c, variant);
+        if (pc)
             for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_pair[s.shape][g < 2 ? g : 0]);
+        t.zpart = dzp;
         fwd_off.push_back(blob.add(&t, sizeof t));
         const int64_t pre[2] = {0, shf[s.shape].ntiles};
         fwd_pre.push_back(blob.add(pre, sizeof pre));
+        std::vector<ReduceTask> zts;
+        if (s.flags & T_ZEXP) {
+            SweepLaunch L{kernel_kind(sh), variant, 0, h->dtype, 1, sh.ntiles, nullptr, nullptr, nullptr};
+            L.pairc = pc;
+            const int64_t g = forward_grid(h, L);
+            for (int r = 0; r < s.nr; ++r)
+                if (s.r[r].phase_pre && s.r[r].layer > 0)
+                    zts.push_back(ReduceTask{dzp, g, kZSlots * kZQ, r * kZQ, h->n,
+                                             dzo + (size_t)(s.r[r].layer - 1) * h->n, 0, 1.0});
+            if ((s.flags & T_READOUT) && p > 0)
+                zts.push_back(ReduceTask{dzp, g, kZSlots * kZQ, kMaxRounds * kZQ, h->n, dzo + (size_t)(p - 1) * h->n, 0, 1.0});
+        }
+        zred_off.push_back(zts.empty() ? 0 : blob.add(zts.data(), zts.size() * sizeof(ReduceTask)));
+        zred_cnt.push_back((int)zts.size());
     }
     for (auto& s : rev) {
         SweepTask t = make_task(h, sha[s.shape], s, 1, s.shape, h->lam, lr, h->tab_r.ptr, p, dpart, objective);
@@ -547,8 +591,12 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
                       reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
-        e = launch_sweep(L, L.pairc ? grid_for(h, L.variant == 2 ? 4 : 3, 0) : grid_for(h, L.kind, 0), h->st);
+        e = launch_sweep(L, forward_grid(h, L), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
+        if (zred_cnt[i]) {
+            e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + zred_off[i]), zred_cnt[i], h->st);
+            if (e != cudaSuccess) return cuda_error(e, "spin expectation reduce");
+        }
     }
     e = launch_reduce(reinterpret_cast<const ReduceTask*>(dblob + rd_off), 1, h->st);
     if (e != cudaSuccess) return cuda_error(e, "readout reduce");
@@ -632,6 +680,29 @@ int qs_evolve(qs_handle h, int p, const double* gamma, const double* beta, int f
     h->theta_pad = (from_plus ? 0.0 : h->theta_pad) + (h->nphys - h->n) * bsum;
     h->have_readout = true;
     return QS_OK;
+}
+
+int qs_evolve_zexp(qs_handle h, int p, const double* gamma, const double* beta, double* zexp) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->inst.valid) return set_error(QS_ESTATE, "qs_evolve_zexp: call qs_set_ising first");
+    if (h->path != QS_PATH_TILED) return set_error(QS_EINVAL, "qs_evolve_zexp: needs the tiled path");
+    if (int rc = check_angles(p, gamma, beta)) return rc;
+    if (p > 0 && !zexp) return set_error(QS_EINVAL, "qs_evolve_zexp: zexp is NULL");
+    if (int rc = prepare_layers(h, p, gamma, beta, true, false, false)) return rc;
+    if (int rc = run_tiled(h, p, true, 0, 0, true)) return rc;
+    cudaError_t e = launch_set_frame(reinterpret_cast<int*>(h->frame.ptr),
+                                     reinterpret_cast<const LayerDev*>(h->layers_f.ptr), p, h->st);
+    if (e != cudaSuccess) return cuda_error(e, "set frame");
+    double bsum = 0;
+    for (int k = 0; k < p; ++k) bsum += beta[k];
+    h->theta_pad = (h->nphys - h->n) * bsum;
+    h->have_readout = true;
+    if (p > 0) {
+        e = cudaMemcpyAsync(zexp, h->zout.ptr, (size_t)p * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return cuda_error(e, "qs_evolve_zexp");
+    }
+    return check_device_error(h);
 }
 
 int qs_readout(qs_handle h, double* E, double* P, double* norm) {

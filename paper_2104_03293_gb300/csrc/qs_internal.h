@@ -44,8 +44,25 @@ enum : int {
     T_READOUT = 2,    // accumulate E, P, norm after the last round
     T_WRITE_LAM = 4,  // write lambda = O psi (adjoint forward pass)
     T_STORE = 8,      // write the tile back (clear only for the last reverse sweep)
-    T_ADJOINT = 16    // two arrays (psi, lambda), gradient accumulation
+    T_ADJOINT = 16,   // two arrays (psi, lambda), gradient accumulation
+    T_ZEXP = 32       // record <Z_q> of the layer ending at each phase point and at the readout
 };
+
+// Per-layer spin expectations <Z_q> (Sec. III.B.2, Fig. 6): every CTA of a
+// T_ZEXP sweep keeps FP64 accumulators in shared memory, one record of kZQ
+// qubits per round (the state after the previous layer, seen at the round's
+// phase) and one for the readout (slot kMaxRounds), and writes them to
+// zpart[blockIdx.x][kZSlots][kZQ] when it exits.
+constexpr int kZQ = 36;                  // qubits per record (>= the largest state)
+constexpr int kZSlots = kMaxRounds + 1;  // records per CTA
+
+// Kernel variants: FULL has every feature; PHASE (middle sweeps with a layer
+// boundary) drops |+> generation, readout and lambda; LEAN (middle sweeps
+// without a phase) also drops the phase.  Leaner variants keep the
+// instruction footprint of the hot loop small.  ZFULL is FULL with the spin
+// expectations of T_ZEXP sweeps; ZPHASE is PHASE with them (the packed-pair
+// kernel; sweep_kernel runs ZPHASE sweeps as ZFULL).
+enum : int { V_FULL = 0, V_PHASE = 1, V_LEAN = 2, V_ZFULL = 3, V_ZPHASE = 4 };
 
 struct SweepRound {
     int layer;       // index into the per-layer parameter array
@@ -76,6 +93,7 @@ struct SweepTask {
     const int32_t* cprog[kMaxLayouts];  // layout programs (build_layout_prog) of the kernel's layouts
     const int32_t* tprog;        // tile program of the shape (build_tile_prog)
     double* partials;            // per tile: np doubles
+    double* zpart;               // T_ZEXP: per CTA kZSlots * kZQ doubles
     int64_t ntiles;
     int64_t part_base;           // first partial slot of this task
     int n, c, g0, flags;

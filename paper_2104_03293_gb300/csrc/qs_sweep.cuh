@@ -126,6 +126,13 @@ struct TMap {
         const uint32_t cm = (1u << c) - 1u, m1 = (1u << n1) - 1u;
         return (uint64_t)(e & cm) | ((uint64_t)((e >> c) & m1) << g0) | ((uint64_t)(e >> (c + n1)) << g1);
     }
+    // tile bit holding global bit q, or -1 when q lies outside the tile
+    __device__ __forceinline__ int tile_bit(int q) const {
+        if (q < c) return q;
+        if (q >= g0 && q < g0 + n1) return c + q - g0;
+        if (q >= g1 && q < g1 + K - c - n1) return c + n1 + q - g1;
+        return -1;
+    }
     __device__ __forceinline__ uint64_t base(int64_t t) const {
         // occupied runs above c in ascending global order: [s1, s1 + l1), [s2, s2 + l2)
         int s1 = g0, l1 = n1, s2 = g1, l2 = K - c - n1;
@@ -294,6 +301,68 @@ __device__ __forceinline__ void warp_sum_to(double v, double* red, int slot, int
 }
 
 // ---------------------------------------------------------------------------
+// Spin expectations <Z_q> = sum_z |psi_z|^2 s_q(z), s_q = 1 - 2 bit_q (the
+// per-qubit magnetisations recorded during AQA, Sec. III.B.2, Fig. 6).
+// ---------------------------------------------------------------------------
+// This thread's share, by tile bit: zv[tb] = sum_m w[m] s_tb over its 2^R
+// amplitudes (w = |psi|^2 in slot m; Map::slot(b) / Map::thr(j) are the tile
+// bits of slot bit b and thread-index bit j), zv[K] = sum_m w[m].
+template <class Map, int K, int R, class F>
+__device__ __forceinline__ void z_thread_sums(const F (&w)[1 << R], uint32_t tid, F (&zv)[K + 1]) {
+    F W = 0;
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) W += w[m];
+    static_for<0, R>([&](auto bc) {
+        constexpr int b = decltype(bc)::value;
+        F hi = 0;  // weight of the slots with bit b set (s = -1)
+#pragma unroll
+        for (int m = 0; m < (1 << R); ++m)
+            if ((m >> b) & 1) hi += w[m];
+        zv[Map::slot(b)] = W - 2 * hi;
+    });
+    static_for<0, K - R>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        zv[Map::thr(j)] = ((tid >> j) & 1u) ? -W : W;
+    });
+    zv[K] = W;
+}
+
+// Sum zv over the CTA and add the tile's contribution to zacc[q], q < nq:
+// a qubit on a tile bit takes that bit's sum, a qubit outside the tile the
+// tile's weight times its spin in the tile's base index; sg = -1 when the
+// stored array is in the flipped frame (every spin negated).  zred holds
+// NW * (K + 1) values.  Called by every thread; the accumulators are FP64 and
+// each CTA adds its tiles in a fixed order, so the sums are reproducible.
+template <int K, int NW, class F>
+__device__ __forceinline__ void z_tile_add(F (&zv)[K + 1], F* zred, double* zacc, const TMap& tm, uint64_t zb,
+                                           int nq, int sg, uint32_t tid) {
+#pragma unroll
+    for (int i = 0; i <= K; ++i) {
+        F v = zv[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        zv[i] = v;
+    }
+    if ((tid & 31u) == 0) {
+#pragma unroll
+        for (int i = 0; i <= K; ++i) zred[(tid >> 5) * (K + 1) + i] = zv[i];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        for (int q = (int)tid; q < nq; q += 32) {
+            const int tb = tm.tile_bit(q);
+            const int col = tb >= 0 ? tb : K;
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) s += (double)zred[w * (K + 1) + col];
+            if (tb < 0 && ((zb >> q) & 1ull)) s = -s;
+            zacc[q] += sg < 0 ? -s : s;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // The sweep
 // ---------------------------------------------------------------------------
 template <class Real, int K, int R, int NA, int KIND>
@@ -315,6 +384,9 @@ struct Sweep {
     static constexpr size_t BUF_BYTES = (size_t)NA * TILE_BYTES;  // one region per array
     static constexpr size_t TT_OFF = BUF_BYTES + 64 + (size_t)NW * NSLOT * 8;  // two TileTabs
     static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    // T_ZEXP kernels: FP64 accumulators [kZSlots][kZQ], then the warp sums
+    static constexpr size_t Z_BYTES = (size_t)kZSlots * kZQ * 8 + (size_t)NW * (K + 1) * sizeof(Real);
+    static_assert(SMEM_BYTES % 8 == 0, "accumulators follow the tile tables");
     static_assert(K - R >= 5, "a tile needs at least one full warp");
     // compile-time tile bits of layout g for SlotCost::init_tile
     template <int g> struct Map {
@@ -461,6 +533,23 @@ struct Sweep {
         gacc += part;
     }
 
+    // ---- spin expectations (single array) -------------------------------------
+    template <int g>
+    __device__ static __forceinline__ void zexp(const C2 (&v)[NA][NS], uint32_t tid, Real* zred, double* zacc,
+                                                const TMap& tm, uint64_t zb, int nq, int sg) {
+        Real w[NS], zv[K + 1];
+#pragma unroll
+        for (int m = 0; m < NS; ++m) w[m] = fma_(v[0][m].x, v[0][m].x, v[0][m].y * v[0][m].y);
+        z_thread_sums<Map<g>, K, R>(w, tid, zv);
+        z_tile_add<K, NW>(zv, zred, zacc, tm, zb, nq, sg, tid);
+    }
+    __device__ static __forceinline__ void zexp_any(int g, const C2 (&v)[NA][NS], uint32_t tid, Real* zred,
+                                                    double* zacc, const TMap& tm, uint64_t zb, int nq, int sg) {
+        if (g == 0) zexp<0>(v, tid, zred, zacc, tm, zb, nq, sg);
+        else if (G > 1 && g == 1) zexp<(G > 1 ? 1 : 0)>(v, tid, zred, zacc, tm, zb, nq, sg);
+        else if (G > 2) zexp<(G > 2 ? 2 : 0)>(v, tid, zred, zacc, tm, zb, nq, sg);
+    }
+
     // global offset of the thread part of layout g
     template <int g>
     __device__ static __forceinline__ uint64_t zthread(uint64_t base, uint32_t tid, const TMap& tm) {
@@ -511,12 +600,6 @@ struct Sweep {
     }
 };
 
-// Kernel variants: FULL has every feature; PHASE (middle sweeps with a layer
-// boundary) drops |+> generation, readout and lambda; LEAN (middle sweeps
-// without a phase) also drops the phase.  Leaner variants keep the
-// instruction footprint of the hot loop small.
-enum : int { V_FULL = 0, V_PHASE = 1, V_LEAN = 2 };
-
 template <class Real, int K, int R, int NA, int KIND, int V>
 __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
     sweep_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks, int64_t total,
@@ -524,15 +607,19 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
     using S = Sweep<Real, K, R, NA, KIND>;
     using C2 = typename S::C2;
     constexpr int NS = S::NS, NW = S::NW, NSLOT = S::NSLOT;
-    constexpr bool kGen = V == V_FULL, kPhase = V != V_LEAN, kRead = V == V_FULL;
+    constexpr bool kZ = V == V_ZFULL && NA == 1;
+    constexpr bool kGen = V == V_FULL || kZ, kPhase = V != V_LEAN, kRead = V == V_FULL || kZ;
     static_assert(KIND != 1 || make_layout(K, R, KIND).regs[0][0] == K - R, "layout 0 holds the top R tile bits");
     extern __shared__ __align__(128) unsigned char smraw[];
     C2* buf = reinterpret_cast<C2*>(smraw);                                      // [NA][2^K]
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + S::BUF_BYTES);
     double* red = reinterpret_cast<double*>(smraw + S::BUF_BYTES + 64);
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);  // [2]: by tile parity
+    double* zacc = reinterpret_cast<double*>(smraw + S::SMEM_BYTES);   // kZ: [kZSlots][kZQ]
+    Real* zred = reinterpret_cast<Real*>(smraw + S::SMEM_BYTES + (size_t)kZSlots * kZQ * 8);
     const uint32_t tid = threadIdx.x;
     C2 v[NA][NS];
+    const bool zon = kZ && (tasks[0].flags & T_ZEXP);  // one task per launch
 
     auto find_task = [&](int64_t gt) -> int {
         if (ntasks == 1) return 0;
@@ -608,6 +695,8 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         mbar_init(full, S::NT);  // one arrival per thread (with its copies, or with the byte count)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (zon)
+        for (int i = (int)tid; i < kZSlots * kZQ; i += S::NT) zacc[i] = 0.0;
     __syncthreads();
     // The CTA's k-th tile: groups of 2^qlog consecutive tiles (which share
     // HBM lines when rows are short) run back to back on one CTA.
@@ -691,6 +780,10 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
             const LayerDev ly = T.layers[rd.layer];
             Real gB = 0, gG = 0;
             const C2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
+            // the state after the previous layer (normalised: the scalars of a
+            // layer's rotations sit in its own phase table)
+            if (zon && rd.phase_pre && rd.layer > 0)
+                S::zexp_any(cur, v, tid, zred, zacc + r * kZQ, tm, base, T.n, ly.frame ? -1 : 1);
             if (kPhase && rd.phase_pre) S::phase_any(cur, v, T, tt, tid, ltab, ly.frame, gG);
             const Real fabs2 = (Real)(ly.fabs * ly.fabs);
             Real fpow = 1;
@@ -716,6 +809,9 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
         }
         if (cur != 0) { transpose(cur, 0); cur = 0; }
 
+        if (zon && (flags & T_READOUT))
+            S::template zexp<0>(v, tid, zred, zacc + kMaxRounds * kZQ, tm, base, T.n,
+                                T.layers[T.end_layer].frame ? -1 : 1);
         if (kRead && (flags & (T_READOUT | T_WRITE_LAM))) {
             const int ef = T.layers[T.end_layer].frame;
             SlotCost<R> sc;
@@ -766,21 +862,33 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
     // land in shared memory the SM hands to a later CTA: report it with the
     // sticky status 2 (the host then refuses to use the handle again).
     if (tid == 0 && pending && !mbar_wait_bounded(full, parity)) atomicMax(err, 2);
+    if (zon) {
+        __syncthreads();
+        double* zp = tasks[0].zpart + (size_t)blockIdx.x * (kZSlots * kZQ);
+        for (int i = (int)tid; i < kZSlots * kZQ; i += S::NT) zp[i] = zacc[i];
+    }
+}
+
+template <class Real, int K, int R, int NA, int KIND, int V>
+constexpr size_t sweep_smem() {
+    using S = Sweep<Real, K, R, NA, KIND>;
+    return S::SMEM_BYTES + (V == V_ZFULL ? S::Z_BYTES : 0);
 }
 
 template <class Real, int K, int R, int NA, int KIND, int V>
 cudaError_t launch_sweep_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
     using S = Sweep<Real, K, R, NA, KIND>;
     auto kern = sweep_kernel<Real, K, R, NA, KIND, V>;
+    constexpr size_t smem = sweep_smem<Real, K, R, NA, KIND, V>();
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     int qlog = 0;
     while ((1 << (qlog + 1)) <= L.group) ++qlog;
-    kern<<<grid, S::NT, S::SMEM_BYTES, st>>>(L.tasks, L.tile_prefix, L.ntasks, L.total_tiles, L.err, qlog);
+    kern<<<grid, S::NT, smem, st>>>(L.tasks, L.tile_prefix, L.ntasks, L.total_tiles, L.err, qlog);
     return note_launch(cudaGetLastError());
 }
 
@@ -788,11 +896,12 @@ template <class Real, int K, int R, int NA, int KIND, int V>
 int grid_cfg() {
     using S = Sweep<Real, K, R, NA, KIND>;
     auto kern = sweep_kernel<Real, K, R, NA, KIND, V>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
+    constexpr size_t smem = sweep_smem<Real, K, R, NA, KIND, V>();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, S::SMEM_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, smem);
     if (per_sm < 1) per_sm = 1;
     return per_sm * sms;
 }

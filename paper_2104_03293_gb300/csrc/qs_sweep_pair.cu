@@ -54,6 +54,9 @@ struct PairSweep {
     static constexpr size_t BUF_BYTES = (size_t)8 << K;
     static constexpr size_t TT_OFF = NB * BUF_BYTES + 64;  // two TileTabs (by tile parity)
     static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    // V_ZPHASE: FP64 spin-expectation accumulators [kZSlots][kZQ], then the warp sums
+    static constexpr size_t Z_BYTES = (size_t)kZSlots * kZQ * 8 + (size_t)(NT / 32) * (K + 1) * 4;
+    static_assert(SMEM_BYTES % 8 == 0, "accumulators follow the tile tables");
     // compile-time tile bits of layout g: slot bit 0 is the pack bit
     template <int g> struct Map {
         __host__ __device__ static constexpr int slot(int b) { return b == 0 ? P : pair_layout(C).regs[g][b - 1]; }
@@ -142,6 +145,21 @@ struct PairSweep {
         }
     }
 
+    // ---- <Z_q> of the tile in layout g: slot m = half | j << 1 ------------------
+    template <int g>
+    __device__ static __forceinline__ void zexp(const float2 (&X)[NJ], const float2 (&Y)[NJ], uint32_t tid,
+                                                float* zred, double* zacc, const TMap& tm, uint64_t zb, int nq,
+                                                int sg) {
+        float w[2 * NJ], zv[K + 1];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            w[2 * j] = fmaf(X[j].x, X[j].x, Y[j].x * Y[j].x);
+            w[2 * j + 1] = fmaf(X[j].y, X[j].y, Y[j].y * Y[j].y);
+        }
+        z_thread_sums<Map<g>, K, 6>(w, tid, zv);
+        z_tile_add<K, NT / 32>(zv, zred, zacc, tm, zb, nq, sg, tid);
+    }
+
     // ---- phase: slot m = lane | j << 1 (cost program of the layout) ------------
     template <int g>
     __device__ static __forceinline__ void phase(float2 (&X)[NJ], float2 (&Y)[NJ], const SweepTask& T,
@@ -177,7 +195,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 // share are fetched once.  Every CTA of a cluster walks the same number of
 // tiles (the tile count and the grid are multiples of four) and passes the
 // barrier once per tile, also after a timed-out wait.
-template <int V> struct PairOcc { static constexpr int value = 3; };  // CTAs per SM (both variants)
+template <int V> struct PairOcc { static constexpr int value = 3; };  // CTAs per SM (every variant)
 
 template <int C, int V, int CL>
 __global__ void __launch_bounds__(128, PairOcc<V>::value)
@@ -185,11 +203,14 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
                       int64_t total, int* __restrict__ err) {
     using S = PairSweep<C>;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NB = S::NB;
-    constexpr bool kPhase = V != V_LEAN;
+    constexpr bool kPhase = V != V_LEAN, kZ = V == V_ZPHASE;
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
+    double* zacc = reinterpret_cast<double*>(smraw + S::SMEM_BYTES);  // kZ: [kZSlots][kZQ]
+    float* zred = reinterpret_cast<float*>(smraw + S::SMEM_BYTES + (size_t)kZSlots * kZQ * 8);
     const uint32_t tid = threadIdx.x;
+    const bool zon = kZ && (tasks[0].flags & T_ZEXP);  // one task per launch
     uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
     float2 X[NJ], Y[NJ];
 
@@ -228,6 +249,8 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         for (int b = 0; b < NB; ++b) mbar_init(full + b, NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (zon)
+        for (int i = (int)tid; i < kZSlots * kZQ; i += NT) zacc[i] = 0.0;
     __syncthreads();
     for (int b = 0; b < NB; ++b) {
         const int64_t g0 = (int64_t)blockIdx.x + (int64_t)b * gridDim.x;
@@ -301,6 +324,13 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             const SweepRound rd = T.rounds[r];
             const LayerDev ly = T.layers[rd.layer];
             const float2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
+            // the state after the previous layer, before this layer's phase
+            if (zon && rd.phase_pre && rd.layer > 0) {
+                double* za = zacc + r * kZQ;
+                const int sg = ly.frame ? -1 : 1;
+                if (cur == 0) S::template zexp<0>(X, Y, tid, zred, za, tm, base, T.n, sg);
+                else S::template zexp<1>(X, Y, tid, zred, za, tm, base, T.n, sg);
+            }
             if (kPhase && rd.phase_pre) do_phase(ltab, ly.frame);
             const float w = (float)ly.w;
             // zig-zag: a round starts in the current layout
@@ -353,17 +383,25 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         for (int q = 0; q < NB; ++q)
             if (((pend >> q) & 1u) && !mbar_wait_bounded(full + q, (phase >> q) & 1u)) atomicMax(err, 2);
     __syncthreads();
+    if (zon) {
+        double* zp = tasks[0].zpart + (size_t)blockIdx.x * (kZSlots * kZQ);
+        for (int i = (int)tid; i < kZSlots * kZQ; i += NT) zp[i] = zacc[i];
+    }
 }
 
 template <int C, int V>
+constexpr size_t pair_smem() { return PairSweep<C>::SMEM_BYTES + (V == V_ZPHASE ? PairSweep<C>::Z_BYTES : 0); }
+
+template <int C, int V>
 static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
+    constexpr size_t smem = pair_smem<C, V>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)PairSweep<C>::SMEM_BYTES);
+                                             (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)PairSweep<C>::SMEM_BYTES);
+                                     (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -371,7 +409,7 @@ static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t 
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(PairSweep<C>::NT);
-        cfg.dynamicSmemBytes = PairSweep<C>::SMEM_BYTES;
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -384,8 +422,8 @@ static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t 
                                            L.total_tiles, L.err);
         return note_launch(e);
     }
-    sweep_pair_kernel<C, V, 1><<<grid, PairSweep<C>::NT, PairSweep<C>::SMEM_BYTES, st>>>(
-        L.tasks, L.tile_prefix, L.ntasks, L.total_tiles, L.err);
+    sweep_pair_kernel<C, V, 1><<<grid, PairSweep<C>::NT, smem, st>>>(L.tasks, L.tile_prefix, L.ntasks,
+                                                                      L.total_tiles, L.err);
     return note_launch(cudaGetLastError());
 }
 
@@ -394,6 +432,8 @@ cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st) {
     if (L.pairc == 2 && L.variant == V_PHASE) return launch_pair_cfg<2, V_PHASE>(L, grid, st);
     if (L.pairc == 3 && L.variant == V_LEAN) return launch_pair_cfg<3, V_LEAN>(L, grid, st);
     if (L.pairc == 3 && L.variant == V_PHASE) return launch_pair_cfg<3, V_PHASE>(L, grid, st);
+    if (L.pairc == 2 && L.variant == V_ZPHASE) return launch_pair_cfg<2, V_ZPHASE>(L, grid, st);
+    if (L.pairc == 3 && L.variant == V_ZPHASE) return launch_pair_cfg<3, V_ZPHASE>(L, grid, st);
     return cudaErrorInvalidValue;
 }
 
@@ -402,11 +442,12 @@ cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st) {
 template <int V>
 static int pair_grid_v() {
     auto kern = sweep_pair_kernel<2, V, 4>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PairSweep<2>::SMEM_BYTES);
+    constexpr size_t smem = pair_smem<2, V>();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(4);
     cfg.blockDim = dim3(PairSweep<2>::NT);
-    cfg.dynamicSmemBytes = PairSweep<2>::SMEM_BYTES;
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 4;
@@ -420,12 +461,15 @@ static int pair_grid_v() {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V, 1>, PairSweep<2>::NT,
-                                                  PairSweep<2>::SMEM_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V, 1>, PairSweep<2>::NT, smem);
     if (per_sm < 1) per_sm = 1;
     return per_sm * sms;
 }
 
-int sweep_pair_grid(int variant) { return variant == V_LEAN ? pair_grid_v<V_LEAN>() : pair_grid_v<V_PHASE>(); }
+int sweep_pair_grid(int variant) {
+    if (variant == V_LEAN) return pair_grid_v<V_LEAN>();
+    if (variant == V_ZPHASE) return pair_grid_v<V_ZPHASE>();
+    return pair_grid_v<V_PHASE>();
+}
 
 }  // namespace qs

@@ -58,6 +58,7 @@ _SIGS = {
     "qs_set_shape_rule": [_P, _I, _I],
     "qs_autotune": [_P, _I, _PI, _PI, _PD],
     "qs_grad": [_P, _I, _PD, _PD, _I, _PD, _PD, _PD],
+    "qs_evolve_zexp": [_P, _I, _PD, _PD, _PD],
     "qs_set_adjoint_buffer": [_P, _P, ctypes.c_size_t],
     "qs_copy_state": [_P, _P, ctypes.c_size_t],
     "qs_state_ptr": [_P, ctypes.POINTER(_P), _PI],
@@ -209,6 +210,13 @@ class State:
     def evolve(self, gamma, beta, from_plus: bool = True):
         g, b = _angles(gamma, beta)
         _check(lib().qs_evolve(self._h, int(g.size), _dptr(g), _dptr(b), int(bool(from_plus))))
+
+    def evolve_zexp(self, gamma, beta) -> np.ndarray:
+        """Evolve from |+>^n and return <Z_i> after every layer, array [p, n]."""
+        g, b = _angles(gamma, beta)
+        out = np.zeros((g.size, self.n))
+        _check(lib().qs_evolve_zexp(self._h, int(g.size), _dptr(g), _dptr(b), _dptr(out)))
+        return out
 
     def readout(self):
         E, P, N = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
