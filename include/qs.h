@@ -285,10 +285,14 @@ const char* qs_version(void);
 /* ------------------------------------------------------------------------ */
 
 /* A batch of `count` independent instances of possibly different n
- * (1..QS_MAX_QUBITS_C64, complex64 only), all on one stream.  Their sweeps run
- * together: each launch covers one sweep of every instance that still has
- * work, so small states fill the GPU.  The library allocates every state.
- * Errors: QS_EINVAL, QS_ENOMEM. */
+ * (1..QS_MAX_QUBITS_C64, complex64 only), all on one stream.  The forward of
+ * the whole batch is one launch of a persistent work-queue kernel over every
+ * tile of every sweep of every instance (ordered sweep by sweep, with a tile
+ * counter per instance ordering its own sweeps); the adjoint's reverse
+ * sweeps are a second launch.  Small states share the GPU with large ones.
+ * One queue holds at most 2^26 tiles of 2^13 amplitudes (evolve and grad
+ * return QS_EINVAL beyond).  The library allocates every state.  Errors:
+ * QS_EINVAL, QS_ENOMEM. */
 int qs_batch_create(qs_batch_handle* out, int count, const int* n, int dtype, void* cuda_stream);
 
 /* Ising cost of instance idx (same rules as qs_set_ising). */
@@ -319,6 +323,17 @@ int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamm
  * qs_batch_results gives E and P_ground at the final angles.  Synchronises. */
 int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2, double eps,
                   double* gamma_io, double* beta_io, int use_graph);
+
+/* Failure-detection test hook (no counterpart in the paper).  Arms the next
+ * qs_batch_evolve to run a work queue in which the second sweep of instance
+ * idx waits for one tile more than its first sweep provides, with a
+ * dependency wait limit of wait_limit_s seconds (0 < limit <= 10): the wait
+ * runs out, the kernel sets its error word and every CTA returns, and the
+ * next call that synchronises (qs_batch_results) returns QS_ETIMEOUT with the
+ * results invalid.  No copy is left in flight, so the batch stays usable:
+ * the next qs_batch_evolve runs the normal plan.  One-shot.  Errors:
+ * QS_EINVAL. */
+int qs_batch_test_withhold(qs_batch_handle b, int idx, double wait_limit_s);
 
 int qs_batch_destroy(qs_batch_handle b);
 

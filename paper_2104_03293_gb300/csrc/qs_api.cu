@@ -136,13 +136,18 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
     }
     for (size_t s = 0; s < shapes[0].size(); ++s) {
         const Shape& sh = shapes[0][s];
-        if (!pair_choice(dtype, 0, sh.kind, sh.c, 1)) continue;
+        const int pc = pair_choice(dtype, 0, sh.kind, sh.c, V_PHASE);
+        if (!pc) continue;
         const PairLayout PL = pair_layout(sh.c);
+        const PairRunsLayout RL = pair_runs_layout();
         for (int g = 0; g < 2; ++g) {
             int slot[6];
-            slot[0] = PL.P;  // slot bit 0: the pack bit; bits 1..5: regs[g]
-            for (int b = 0; b < 5; ++b) slot[1 + b] = PL.regs[g][b];
-            prog_pair[s][g] = add(build_layout_prog(sh, I.ei, I.ej, I.J, slot, 6, PL.tbits[g], 7));
+            slot[0] = pc == 1 ? 0 : PL.P;  // slot bit 0: the pack bit; bits 1..5: regs[g]
+            for (int b = 0; b < 5; ++b) slot[1 + b] = pc == 1 ? RL.regs[g][b] : PL.regs[g][b];
+            const int* tb = pc == 1 ? RL.tbits[g] : PL.tbits[g];
+            const std::vector<int32_t> lp = build_layout_prog(sh, I.ei, I.ej, I.J, slot, 6, tb, 7);
+            for (int m = 0; m < 64; ++m) pair_q[s].q[g][m] = lp[m];
+            prog_pair[s][g] = add(lp);
         }
     }
     for (size_t s = 0; s < shapes[1].size(); ++s) {
@@ -154,7 +159,9 @@ int Instance::set(int n_, int nphys_, int dtype_, const double* hfield, int n_ed
             int slot[5];
             slot[0] = PL.P;  // slot bit 0: the pack bit; bits 1..4: regs[g]
             for (int b = 0; b < 4; ++b) slot[1 + b] = PL.regs[g][b];
-            prog_pair_adj[s][g] = add(build_layout_prog(sh, I.ei, I.ej, I.J, slot, 5, PL.tbits[g], 8));
+            const std::vector<int32_t> lp = build_layout_prog(sh, I.ei, I.ej, I.J, slot, 5, PL.tbits[g], 8);
+            for (int m = 0; m < 32; ++m) pair_adj_q[s].q[g][m] = lp[m];
+            prog_pair_adj[s][g] = add(lp);
         }
     }
     {
@@ -217,7 +224,7 @@ struct qs_state {
     Uploader up, up_ang;
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
-    int grid[2][6] = {};  // [adjoint][kernel kind; 3, 4, 5 = packed-pair kernel, phase / lean / zexp]
+    int grid[2][7] = {};  // [adjoint][kernel kind; 3, 4, 5 = packed-pair kernel, phase / lean / zexp; 6 = runs]
     bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
     int device = 0;
     ShapeRule rule;                      // tile-shape plan (qs_set_shape_rule / qs_autotune)
@@ -403,15 +410,19 @@ int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_
 static int grid_for(qs_handle h, int kind, int adjoint) {
     int& g = h->grid[adjoint][kind];
     if (!g)
-        g = kind < 3 ? sweep_grid(h->dtype, adjoint, kind)
-                     : (adjoint ? sweep_pair_adj_grid() : sweep_pair_grid(kind == 4 ? V_LEAN : kind == 5 ? V_ZPHASE : V_PHASE));
+        g = kind < 3    ? sweep_grid(h->dtype, adjoint, kind)
+            : adjoint   ? sweep_pair_adj_grid()
+            : kind == 6 ? sweep_runs_grid(V_PHASE)
+                        : sweep_pair_grid(kind == 4 ? V_LEAN : kind == 5 ? V_ZPHASE : V_PHASE);
     return g;
 }
 
 // Grid of a forward sweep launch (the persistent grid, clamped as in
 // launch_sweep to the number of tiles).
 static int forward_grid(qs_handle h, const SweepLaunch& L) {
-    int g = L.pairc ? grid_for(h, L.variant == V_LEAN ? 4 : L.variant == V_ZPHASE ? 5 : 3, 0) : grid_for(h, L.kind, 0);
+    int g = L.pairc == 1 ? grid_for(h, 6, 0)
+            : L.pairc    ? grid_for(h, L.variant == V_LEAN ? 4 : L.variant == V_ZPHASE ? 5 : 3, 0)
+                         : grid_for(h, L.kind, 0);
     if (g > L.total_tiles) g = (int)L.total_tiles;
     return g < 1 ? 1 : g;
 }
@@ -511,7 +522,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
             if (rec) s.flags |= T_ZEXP;
         }
         int gmax = 1;
-        for (int k = 0; k < 6; ++k) gmax = std::max(gmax, k < 3 ? grid_for(h, k, 0) : (h->dtype == 0 ? grid_for(h, k, 0) : 1));
+        for (int k = 0; k < 7; ++k) gmax = std::max(gmax, k < 3 ? grid_for(h, k, 0) : (h->dtype == 0 ? grid_for(h, k, 0) : 1));
         if (int rc = h->zpart.reserve((size_t)gmax * kZSlots * kZQ * sizeof(double))) return rc;
         if (int rc = h->zout.reserve((size_t)std::max(p, 1) * h->n * sizeof(double))) return rc;
     }
@@ -591,6 +602,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
                       reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
+        L.pq = &I.pair_q[fwd[i].shape];
         e = launch_sweep(L, forward_grid(h, L), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
         if (zred_cnt[i]) {
@@ -605,6 +617,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         SweepLaunch L{kernel_kind(sh), 0, 1, h->dtype, 1, sh.ntiles, reinterpret_cast<const SweepTask*>(dblob + rev_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + rev_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 1, sh.kind, sh.c, 0);
+        L.paq = &I.pair_adj_q[rev[i].shape];
         e = launch_sweep(L, grid_for(h, L.pairc ? 3 : L.kind, 1), h->st);
         if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
         if (red_cnt[i]) {

@@ -60,6 +60,8 @@ struct Instance {
     size_t tprog_off[2][kMaxShapes] = {};              // tile programs of the shapes
     size_t prog_pair[kMaxShapes][2] = {};              // packed-pair layouts (forward shapes)
     size_t prog_pair_adj[kMaxShapes][3] = {};          // packed-pair adjoint layouts (adjoint shapes)
+    PairQ pair_q[kMaxShapes] = {};                     // host copies of the packed-pair forward Q tables
+    PairAdjQ pair_adj_q[kMaxShapes] = {};              // and of the adjoint ones
     size_t enum_off = 0, plain_off = 0;
     int plain_nf = 0, plain_ne = 0, plain_const0 = 0;
     DevBuf progs;

@@ -1,12 +1,15 @@
 // C ABI of include/qs.h: batched instances.
 //
-// Every instance keeps its own tile shapes and zig-zag sweep list.  Sweeps run
-// in waves: wave w is the w-th sweep of every instance that has one, issued as
-// at most one launch per tile size, each launch a list of tasks over which the
-// persistent CTAs stride.  Small states therefore share the GPU instead of
-// each leaving most SMs idle.  The whole optimiser step (preparation, forward
-// waves, reverse waves, reductions, Adam) has static launch parameters, so it
-// can be captured once in a CUDA graph and replayed.
+// Every instance keeps its own tile shapes and zig-zag sweep list.  A forward
+// of the whole batch is one launch of the persistent work-queue kernel
+// (qs_queue.cu) over the tiles of every sweep of every instance, ordered wave
+// by wave (the w-th sweep of each instance, then the next), with one tile
+// counter per instance ordering an instance's sweeps; the adjoint's reverse
+// sweeps are a second such launch.  Small states therefore share the GPU
+// with large ones, and instances with few layers leave no idle waves.  The
+// whole optimiser step (preparation, forward queue, reverse queue,
+// reductions, Adam) has static launch parameters, so it can be captured once
+// in a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,17 +25,18 @@ using namespace qs;
 
 namespace {
 
-struct Launch {
-    int kind, adjoint, variant, group;
-    int ntasks;
-    int64_t total_tiles;
-    size_t task_off, pre_off;  // byte offsets in the uploaded blob
-};
+// Dependency wait limit of the queue kernel (device time).
+constexpr uint64_t kQueueWaitNs = 4000000000ull;
+// Tiles of one work-queue launch (its item -> task table holds 4 bytes each).
+constexpr int64_t kQueueMaxTiles = (int64_t)1 << 26;
 
-struct Wave {
-    std::vector<Launch> launches;
-    size_t red_off = 0;
-    int nred = 0;
+// One work-queue launch: its task list, tile prefix and reductions.
+struct QueuePlan {
+    int ntasks = 0;
+    int64_t total = 0;
+    size_t task_off = 0, pre_off = 0, red_off = 0, seg_off = 0;  // byte offsets in the uploaded blob
+    size_t item_off = 0, dn_off = 0;                             // item -> task table, (dep, need) per task
+    int nred = 0, nseg = 0;  // reductions, grouped into segments by output
 };
 
 struct Blob {
@@ -64,19 +68,22 @@ struct qs_batch {
     std::vector<size_t> lay_off, tab_off;  // per instance: LayerDev index / table element offsets
     Uploader up;
     // plans (device blob in up.dev)
-    std::vector<Wave> fwd_waves, rev_waves;
+    QueuePlan fwd_q, rev_q;
+    DevBuf qctl;  // queue counter (u64) + per-instance tile counters (u32), zeroed per launch
     size_t prep_f_off = 0, prep_r_off = 0;
     bool plan_grad = false, planned = false;
-    int grid[2][3] = {};  // [adjoint][kernel kind]
+    int grid[2] = {};  // [adjoint]: persistent queue grid
+    uint64_t wait_ns = kQueueWaitNs;  // dependency wait limit
+    int withhold = -1;  // failure-detection test: the instance whose dependency is withheld
     cudaGraphExec_t graph = nullptr;
     bool have_results = false;
     bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
     int objective = 0;
 };
 
-static int bgrid(qs_batch_handle b, int kind, int adjoint) {
-    int& g = b->grid[adjoint][kind];
-    if (!g) g = sweep_grid(b->dtype, adjoint, kind);
+static int bgrid(qs_batch_handle b, int adjoint) {
+    int& g = b->grid[adjoint];
+    if (!g) g = queue_grid(adjoint);
     return g;
 }
 
@@ -146,7 +153,10 @@ int qs_batch_set_ising(qs_batch_handle b, int idx, const double* hfield, int n_e
     if (idx < 0 || idx >= b->count) return set_error(QS_EINVAL, "qs_batch_set_ising: idx %d out of range", idx);
     cudaSetDevice(b->device);
     Instance tmp;
-    if (int rc = tmp.set(b->n[idx], b->nphys[idx], b->dtype, hfield, n_edges, edges, J, b->st, b->enum_scratch))
+    // contiguous shape A for every size: the queue kernel serves contiguous
+    // and strided tiles
+    if (int rc = tmp.set(b->n[idx], b->nphys[idx], b->dtype, hfield, n_edges, edges, J, b->st, b->enum_scratch,
+                         ShapeRule{0, -1}))
         return rc;
     b->inst[idx] = std::move(tmp);
     b->planned = false;
@@ -156,7 +166,7 @@ int qs_batch_set_ising(qs_batch_handle b, int idx, const double* hfield, int n_e
 
 }  // extern "C"
 
-// Build the wave plan and the layer / table buffers for the current p[].
+// Build the queue plans and the layer / table buffers for the current p[].
 static int build_plan(qs_batch_handle b, bool grad, int objective) {
     const int C = b->count;
     // layer and table offsets
@@ -203,114 +213,132 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
     const float2* tr = reinterpret_cast<const float2*>(b->tab_r.ptr);
 
     Blob blob;
-    size_t part_need = 0;
-    double* dpart = nullptr;  // patched below after sizing: tasks store offsets relative to it
-    // first pass: size partials per wave
-    auto wave_partials = [&](const std::vector<std::vector<PlanSweep>>& L, size_t w, int cfgi) {
+    // partials: one block per task with readout or adjoint sums (the forward
+    // queue's reductions run before the reverse queue reuses the buffer)
+    auto queue_partials = [&](const std::vector<std::vector<PlanSweep>>& L, int cfgi) {
         size_t need = 0;
-        for (int i = 0; i < C; ++i) {
-            if (w >= L[i].size()) continue;
-            const PlanSweep& s = L[i][w];
-            const Shape& sh = b->inst[i].shapes[cfgi][s.shape];
-            const int np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
-            need += (size_t)sh.ntiles * np;
-        }
+        for (int i = 0; i < C; ++i)
+            for (const PlanSweep& s : L[i]) {
+                const Shape& sh = b->inst[i].shapes[cfgi][s.shape];
+                const int np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
+                need += (size_t)sh.ntiles * np;
+            }
         return need;
     };
-    for (size_t w = 0; w < maxf; ++w) part_need = std::max(part_need, wave_partials(fwd, w, 0));
-    for (size_t w = 0; w < maxr; ++w) part_need = std::max(part_need, wave_partials(rev, w, 1));
+    const size_t part_need = std::max(queue_partials(fwd, 0), grad ? queue_partials(rev, 1) : size_t(0));
     if (int rc = b->partials.reserve((part_need + 4) * sizeof(double))) return rc;
-    dpart = reinterpret_cast<double*>(b->partials.ptr);
+    double* dpart = reinterpret_cast<double*>(b->partials.ptr);
+    if (int rc = b->qctl.reserve(64 + (size_t)C * sizeof(unsigned))) return rc;
 
-    auto build_waves = [&](const std::vector<std::vector<PlanSweep>>& L, size_t nw, int adj, std::vector<Wave>& out) {
-        out.clear();
+    // the task list of one queue, wave by wave; task (i, w) needs every tile
+    // of instance i's sweeps 0..w-1
+    auto build_queue = [&](const std::vector<std::vector<PlanSweep>>& L, size_t nw, int adj, QueuePlan& out) {
+        std::vector<SweepTask> tasks;
+        std::vector<int64_t> pre{0}, need(C, 0);
+        std::vector<ReduceTask> rts;
+        int64_t pbase = 0;
         for (size_t w = 0; w < nw; ++w) {
-            Wave wave;
-            int64_t pbase = 0;
-            std::vector<ReduceTask> rts;
-            for (int kind = 0; kind < 3; ++kind) {
-                std::vector<SweepTask> tasks;
-                std::vector<int64_t> pre{0};
-                int variant = 2;  // leanest kernel that serves every task of the launch
-                for (int i = 0; i < C; ++i) {
-                    if (w >= L[i].size()) continue;
-                    const PlanSweep& s = L[i][w];
-                    const Instance& I = b->inst[i];
-                    const Shape& sh = I.shapes[adj][s.shape];
-                    if (kernel_kind(sh) != kind) continue;
-                    variant = std::min(variant, sweep_variant(s.flags, s.nr, s.r));
-                    SweepTask t;
-                    std::memset(&t, 0, sizeof t);
-                    t.psi = states + b->st_off[i];
-                    t.lam = lams ? lams + b->st_off[i] : nullptr;
-                    t.layers = (adj ? lr : lf) + b->lay_off[i];
-                    t.tab = (adj ? tr : tf) + b->tab_off[i];
-                    for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_off[adj][s.shape][g]);
-                    t.tprog = I.prog(I.tprog_off[adj][s.shape]);
-                    t.partials = dpart;
-                    t.ntiles = sh.ntiles;
-                    t.part_base = 0;
-                    t.n = b->nphys[i];
-                    t.c = sh.c;
-                    t.g0 = sh.g0;
-                    t.flags = s.flags;
-                    t.nrounds = s.nr;
-                    t.objective = objective;
-                    t.tab_stride = I.range;
-                    t.cost_lo = I.cost_lo;
-                    t.gidx = (int)(I.cmin - I.cost_lo);
-                    t.end_layer = b->p[i];
-                    t.amp0 = std::pow(2.0, -0.5 * b->nphys[i]);
-                    t.np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
-                    for (int r = 0; r < s.nr; ++r) t.rounds[r] = s.r[r];
-                    t.kind = sh.kind;
-                    t.n1 = sh.n1;
-                    t.g1 = sh.g1;
-                    // partial slots of this task: [pbase, pbase + ntiles) in units of np doubles
-                    const double* tp = dpart + pbase;
-                    if (t.np) {
-                        // store pointer shifted so that (part_base + tile) * np indexes this task's block
-                        t.partials = dpart + pbase;
-                    }
-                    const double sc = std::ldexp(1.0, -I.shift);
-                    if (s.flags & T_READOUT) {
-                        rts.push_back(ReduceTask{tp, sh.ntiles, 3, 0, 1, dout + 3 * i, 0, sc});
-                        rts.push_back(ReduceTask{tp, sh.ntiles, 3, 1, 2, dout + 3 * i + 1, 0, 1.0});
-                    }
-                    if (s.flags & T_ADJOINT) {
-                        const double lam_sc = objective == QS_OBJ_ENERGY ? sc : 1.0;
-                        for (int r = 0; r < s.nr; ++r) {
-                            const int Ly = s.r[r].layer;
-                            double* db = dgr + b->total + b->aoff[i] + Ly;
-                            double* dg = dgr + b->aoff[i] + Ly;
-                            rts.push_back(ReduceTask{tp, sh.ntiles, 2 * s.nr, 2 * r, 1, db, 1, 2.0 * lam_sc});
-                            if (s.r[r].phase_post)
-                                rts.push_back(ReduceTask{tp, sh.ntiles, 2 * s.nr, 2 * r + 1, 1, dg, 1, 2.0 * sc * lam_sc});
-                        }
-                    }
-                    pbase += (int64_t)sh.ntiles * t.np;
-                    tasks.push_back(t);
-                    pre.push_back(pre.back() + sh.ntiles);
+            for (int i = 0; i < C; ++i) {
+                if (w >= L[i].size()) continue;
+                const PlanSweep& s = L[i][w];
+                const Instance& I = b->inst[i];
+                const Shape& sh = I.shapes[adj][s.shape];
+                SweepTask t;
+                std::memset(&t, 0, sizeof t);
+                t.psi = states + b->st_off[i];
+                t.lam = lams ? lams + b->st_off[i] : nullptr;
+                t.layers = (adj ? lr : lf) + b->lay_off[i];
+                t.tab = (adj ? tr : tf) + b->tab_off[i];
+                for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_off[adj][s.shape][g]);
+                t.tprog = I.prog(I.tprog_off[adj][s.shape]);
+                t.ntiles = sh.ntiles;
+                t.part_base = 0;
+                t.n = b->nphys[i];
+                t.c = sh.c;
+                t.g0 = sh.g0;
+                t.flags = s.flags;
+                bool tab = (s.flags & (T_READOUT | T_WRITE_LAM)) != 0;
+                for (int r = 0; r < s.nr; ++r) tab = tab || s.r[r].phase_pre || s.r[r].phase_post;
+                if (tab) t.flags |= T_TAB;
+                t.nrounds = s.nr;
+                t.objective = objective;
+                t.tab_stride = I.range;
+                t.cost_lo = I.cost_lo;
+                t.gidx = (int)(I.cmin - I.cost_lo);
+                t.end_layer = b->p[i];
+                t.amp0 = std::pow(2.0, -0.5 * b->nphys[i]);
+                t.np = (s.flags & T_ADJOINT) ? 2 * s.nr : ((s.flags & T_READOUT) ? 3 : 0);
+                for (int r = 0; r < s.nr; ++r) t.rounds[r] = s.r[r];
+                t.kind = sh.kind;
+                t.n1 = sh.n1;
+                t.g1 = sh.g1;
+                t.dep = i;
+                t.need = need[i];
+                if (adj == 0 && w == 1 && i == b->withhold) t.need += 1;  // never satisfied: the wait runs out
+                need[i] += sh.ntiles;
+                // this task's partial block: (part_base + tile) * np indexes it
+                const double* tp = dpart + pbase;
+                t.partials = dpart + pbase;
+                const double sc = std::ldexp(1.0, -I.shift);
+                if (s.flags & T_READOUT) {
+                    rts.push_back(ReduceTask{tp, sh.ntiles, 3, 0, 1, dout + 3 * i, 0, sc});
+                    rts.push_back(ReduceTask{tp, sh.ntiles, 3, 1, 2, dout + 3 * i + 1, 0, 1.0});
                 }
-                if (tasks.empty()) continue;
-                Launch l;
-                l.kind = kind;
-                l.adjoint = adj;
-                l.variant = variant;
-                l.group = 1;
-                l.ntasks = (int)tasks.size();
-                l.total_tiles = pre.back();
-                l.task_off = blob.add(tasks.data(), tasks.size() * sizeof(SweepTask));
-                l.pre_off = blob.add(pre.data(), pre.size() * sizeof(int64_t));
-                wave.launches.push_back(l);
+                if (s.flags & T_ADJOINT) {
+                    const double lam_sc = objective == QS_OBJ_ENERGY ? sc : 1.0;
+                    for (int r = 0; r < s.nr; ++r) {
+                        const int Ly = s.r[r].layer;
+                        double* db = dgr + b->total + b->aoff[i] + Ly;
+                        double* dg = dgr + b->aoff[i] + Ly;
+                        rts.push_back(ReduceTask{tp, sh.ntiles, 2 * s.nr, 2 * r, 1, db, 1, 2.0 * lam_sc});
+                        if (s.r[r].phase_post)
+                            rts.push_back(ReduceTask{tp, sh.ntiles, 2 * s.nr, 2 * r + 1, 1, dg, 1, 2.0 * sc * lam_sc});
+                    }
+                }
+                pbase += (int64_t)sh.ntiles * t.np;
+                tasks.push_back(t);
+                pre.push_back(pre.back() + sh.ntiles);
             }
-            wave.nred = (int)rts.size();
-            wave.red_off = rts.empty() ? 0 : blob.add(rts.data(), rts.size() * sizeof(ReduceTask));
-            out.push_back(wave);
         }
+        out.ntasks = (int)tasks.size();
+        out.total = pre.back();
+        out.task_off = tasks.empty() ? 0 : blob.add(tasks.data(), tasks.size() * sizeof(SweepTask));
+        out.pre_off = blob.add(pre.data(), pre.size() * sizeof(int64_t));
+        std::vector<int> item_task((size_t)out.total);
+        std::vector<int2> dn(tasks.size());
+        for (size_t k = 0; k < tasks.size(); ++k) {
+            for (int64_t it = pre[k]; it < pre[k + 1]; ++it) item_task[(size_t)it] = (int)k;
+            dn[k] = make_int2(tasks[k].dep, (int)tasks[k].need);
+        }
+        out.item_off = item_task.empty() ? 0 : blob.add(item_task.data(), item_task.size() * sizeof(int));
+        out.dn_off = dn.empty() ? 0 : blob.add(dn.data(), dn.size() * sizeof(int2));
+        // every output (an instance's E, P or one angle derivative) gets the
+        // sums of several tasks (one per tile shape): group them by output,
+        // in plan order, so that one block adds them in a fixed order
+        std::stable_sort(rts.begin(), rts.end(),
+                         [](const ReduceTask& a, const ReduceTask& b2) { return a.out < b2.out; });
+        std::vector<int> seg{0};
+        for (size_t k = 1; k < rts.size(); ++k)
+            if (rts[k].out != rts[k - 1].out) seg.push_back((int)k);
+        seg.push_back((int)rts.size());
+        out.nred = (int)rts.size();
+        out.nseg = rts.empty() ? 0 : (int)seg.size() - 1;
+        out.red_off = rts.empty() ? 0 : blob.add(rts.data(), rts.size() * sizeof(ReduceTask));
+        out.seg_off = rts.empty() ? 0 : blob.add(seg.data(), seg.size() * sizeof(int));
     };
-    build_waves(fwd, maxf, 0, b->fwd_waves);
-    build_waves(rev, maxr, 1, b->rev_waves);
+    // the item -> task table (4 bytes per tile of every sweep) bounds a queue
+    auto queue_tiles = [&](const std::vector<std::vector<PlanSweep>>& L, int cfgi) {
+        int64_t t = 0;
+        for (int i = 0; i < C; ++i)
+            for (const PlanSweep& s : L[i]) t += b->inst[i].shapes[cfgi][s.shape].ntiles;
+        return t;
+    };
+    if (queue_tiles(fwd, 0) > kQueueMaxTiles || (grad && queue_tiles(rev, 1) > kQueueMaxTiles))
+        return set_error(QS_EINVAL, "batch too large: more than %lld tiles in one work queue; split the batch",
+                         (long long)kQueueMaxTiles);
+    build_queue(fwd, maxf, 0, b->fwd_q);
+    if (grad) build_queue(rev, maxr, 1, b->rev_q);
+    else b->rev_q = QueuePlan{};
 
     // preparation tasks (angles live in b->angles: [gamma_all, beta_all])
     const double* da = reinterpret_cast<const double*>(b->angles.ptr);
@@ -335,26 +363,34 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
     return QS_OK;
 }
 
-static int run_waves(qs_batch_handle b, const std::vector<Wave>& waves) {
+static int run_queue(qs_batch_handle b, const QueuePlan& q, int adjoint) {
+    if (q.ntasks == 0) return QS_OK;
     const unsigned char* d = reinterpret_cast<const unsigned char*>(b->up.dev.ptr);
-    for (const Wave& w : waves) {
-        for (const Launch& l : w.launches) {
-            SweepLaunch L{l.kind, l.variant, l.adjoint, b->dtype, l.ntasks, l.total_tiles,
-                          reinterpret_cast<const SweepTask*>(d + l.task_off),
-                          reinterpret_cast<const int64_t*>(d + l.pre_off), reinterpret_cast<int*>(b->err.ptr),
-                          l.group};
-            cudaError_t e = launch_sweep(L, bgrid(b, l.kind, l.adjoint), b->st);
-            if (e != cudaSuccess) return cuda_error(e, "batched sweep");
-        }
-        if (w.nred) {
-            cudaError_t e = launch_reduce(reinterpret_cast<const ReduceTask*>(d + w.red_off), w.nred, b->st);
-            if (e != cudaSuccess) return cuda_error(e, "batched reduce");
-        }
+    unsigned char* ctl = reinterpret_cast<unsigned char*>(b->qctl.ptr);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, 64 + (size_t)b->count * sizeof(unsigned), b->st);
+    if (e != cudaSuccess) return cuda_error(e, "queue counters");
+    QueueLaunch Q{adjoint,
+                  q.ntasks,
+                  q.total,
+                  reinterpret_cast<const SweepTask*>(d + q.task_off),
+                  reinterpret_cast<const int64_t*>(d + q.pre_off),
+                  reinterpret_cast<const int*>(d + q.item_off),
+                  reinterpret_cast<const int2*>(d + q.dn_off),
+                  reinterpret_cast<unsigned long long*>(ctl),
+                  reinterpret_cast<unsigned*>(ctl + 64),
+                  reinterpret_cast<int*>(b->err.ptr),
+                  b->wait_ns};
+    e = launch_queue(Q, bgrid(b, adjoint), b->st);
+    if (e != cudaSuccess) return cuda_error(e, "batched queue sweep");
+    if (q.nseg) {
+        e = launch_reduce_seg(reinterpret_cast<const ReduceTask*>(d + q.red_off),
+                              reinterpret_cast<const int*>(d + q.seg_off), q.nseg, b->st);
+        if (e != cudaSuccess) return cuda_error(e, "batched reduce");
     }
     return QS_OK;
 }
 
-// One evaluation on the device angles: prep, forward waves (+ reverse waves).
+// One evaluation on the device angles: prep, forward queue (+ reverse queue).
 static int run_step(qs_batch_handle b, bool grad) {
     const unsigned char* d = reinterpret_cast<const unsigned char*>(b->up.dev.ptr);
     cudaError_t e = launch_prep_batch(b->dtype, reinterpret_cast<const PrepTask*>(d + b->prep_f_off), b->count, b->st);
@@ -365,9 +401,9 @@ static int run_step(qs_batch_handle b, bool grad) {
         e = cudaMemsetAsync(b->grads.ptr, 0, (size_t)2 * b->total * sizeof(double), b->st);
         if (e != cudaSuccess) return cuda_error(e, "zero grads");
     }
-    if (int rc = run_waves(b, b->fwd_waves)) return rc;
+    if (int rc = run_queue(b, b->fwd_q, 0)) return rc;
     if (grad)
-        if (int rc = run_waves(b, b->rev_waves)) return rc;
+        if (int rc = run_queue(b, b->rev_q, 1)) return rc;
     return QS_OK;
 }
 
@@ -419,8 +455,25 @@ int qs_batch_evolve(qs_batch_handle b, const int* p, const int64_t* angle_off, c
     if (int rc = upload_angles(b)) return rc;
     if (!b->planned || b->plan_grad)
         if (int rc = build_plan(b, false, 0)) return rc;
-    if (int rc = run_step(b, false)) return rc;
+    int rc = run_step(b, false);
+    if (b->withhold >= 0) {  // one-shot failure-detection test: back to the normal plan and limit
+        b->withhold = -1;
+        b->wait_ns = kQueueWaitNs;
+        b->planned = false;
+    }
+    if (rc) return rc;
     b->have_results = true;
+    return QS_OK;
+}
+
+int qs_batch_test_withhold(qs_batch_handle b, int idx, double wait_limit_s) {
+    if (int rc = check_batch(b)) return rc;
+    if (idx < 0 || idx >= b->count) return set_error(QS_EINVAL, "qs_batch_test_withhold: bad instance %d", idx);
+    if (!(wait_limit_s > 0.0 && wait_limit_s <= 10.0))
+        return set_error(QS_EINVAL, "qs_batch_test_withhold: wait limit must lie in (0, 10] s");
+    b->withhold = idx;
+    b->wait_ns = (uint64_t)(wait_limit_s * 1e9);
+    b->planned = false;
     return QS_OK;
 }
 

@@ -45,7 +45,8 @@ enum : int {
     T_WRITE_LAM = 4,  // write lambda = O psi (adjoint forward pass)
     T_STORE = 8,      // write the tile back (clear only for the last reverse sweep)
     T_ADJOINT = 16,   // two arrays (psi, lambda), gradient accumulation
-    T_ZEXP = 32       // record <Z_q> of the layer ending at each phase point and at the readout
+    T_ZEXP = 32,      // record <Z_q> of the layer ending at each phase point and at the readout
+    T_TAB = 64        // work queue: the tile needs its cost table (a phase or a readout)
 };
 
 // Per-layer spin expectations <Z_q> (Sec. III.B.2, Fig. 6): every CTA of a
@@ -103,7 +104,21 @@ struct SweepTask {
     int end_layer;               // layers[end_layer].frame = frame after the last round
     double amp0;                 // 2^{-n/2} for T_GEN
     int np;                      // doubles per tile in partials
+    int dep;                     // work queue: the instance whose tile counter orders this task
+    int64_t need;                // work queue: tiles of that instance to complete before any tile of this task
     SweepRound rounds[kMaxRounds];
+};
+
+// Intra-register coupling tables Q[m] of the two packed-pair forward layouts
+// of one tile shape, passed to the kernel by value (kernel parameters sit in
+// the constant bank, so each compile-time Q[g][m] is an instruction operand).
+struct PairQ {
+    int32_t q[2][64];
+};
+
+// The same for the three packed-pair adjoint layouts (2^5 slots each).
+struct PairAdjQ {
+    int32_t q[3][32];
 };
 
 // A sweep over a list of tasks (one tile shape per launch).
@@ -119,6 +134,8 @@ struct SweepLaunch {
     int* err;                      // device error word (set on a timed-out wait)
     int group = 1;                 // consecutive tiles per CTA turn (a power of 2)
     int pairc = 0;                 // 2 or 3: packed-pair kernel for carried bits c (qs_pair.h)
+    const PairQ* pq = nullptr;     // host: Q tables of the shape (packed-pair forward sweeps)
+    const PairAdjQ* paq = nullptr; // host: Q tables of the shape (packed-pair adjoint sweeps)
 };
 
 // Cost program: the Ising cost of Eq. (HC) specialised to one register layout.
@@ -136,9 +153,13 @@ cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st);
 cudaError_t launch_sweep_pair_adj(const SweepLaunch& L, int grid, cudaStream_t st);
 int sweep_pair_adj_grid();
 int sweep_pair_grid(int variant);  // variant as sweep_variant: 1 phase, 2 rotations only
+// Packed-pair forward sweep of the run-structured shape A (V_PHASE, V_LEAN).
+cudaError_t launch_sweep_runs(const SweepLaunch& L, int grid, cudaStream_t st);
+int sweep_runs_grid(int variant);
 // Packed-pair kernel choice for a sweep, else 0: the carried-bit count c (2
 // or 3) for a strided complex64 sweep (forward: without readout; adjoint:
-// every reverse sweep), 1 for an adjoint sweep of the run-structured shape A.
+// every reverse sweep), 1 for a sweep of the run-structured shape A (adjoint:
+// every reverse sweep; forward: without |+> generation or readout).
 int pair_choice(int dtype, int adjoint, int kind, int c, int variant);
 // ---------------------------------------------------------------------------
 // Launch accounting (qs_launch_count): every launcher reports its kernels.
@@ -146,6 +167,26 @@ cudaError_t note_launch(cudaError_t e, int kernels = 1);
 int64_t launch_total();
 
 cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st);
+
+// Persistent work queue over every tile of every task of a batch (complex64,
+// kinds 0 and 1): CTAs take tiles in task order from the counter *next; a
+// tile of task t starts once done[t.dep] >= t.need (a bounded wait of
+// wait_ns, reported through err) and adds one to done[t.dep] when stored.
+struct QueueLaunch {
+    int adjoint;
+    int ntasks;
+    int64_t total_tiles;
+    const SweepTask* tasks;           // device
+    const int64_t* tile_prefix;       // device, ntasks + 1
+    const int* item_task;             // device, total_tiles: the task of every item
+    const int2* depneed;              // device, ntasks: (dep, need) of every task
+    unsigned long long* next;         // device, zeroed before the launch
+    unsigned int* done;               // device, one per instance, zeroed before the launch
+    int* err;
+    uint64_t wait_ns;
+};
+cudaError_t launch_queue(const QueueLaunch& Q, int grid, cudaStream_t st);
+int queue_grid(int adjoint);
 int sweep_grid(int dtype, int adjoint, int kind);   // persistent grid size
 // Leanest kernel variant that can run a sweep with these flags and rounds.
 int sweep_variant(int flags, int nrounds, const SweepRound* rounds);
@@ -174,6 +215,9 @@ struct ReduceTask {
     double mult;             // out (+)= mult * sum
 };
 cudaError_t launch_reduce(const ReduceTask* tasks, int ntasks, cudaStream_t st);
+// Block b reduces tasks [seg[b], seg[b + 1]) in order (tasks sharing an
+// output must sit in one segment).
+cudaError_t launch_reduce_seg(const ReduceTask* tasks, const int* seg, int nseg, cudaStream_t st);
 
 // Full-enumeration ground-state search of a cost program with register bits
 // 0..5 over 2^n states: writes (cmin, cmax, argmin, count) as int64 into out.

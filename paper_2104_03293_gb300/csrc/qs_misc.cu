@@ -170,6 +170,37 @@ cudaError_t launch_reduce(const ReduceTask* tasks, int ntasks, cudaStream_t st) 
     return note_launch(cudaGetLastError());
 }
 
+// Segmented: block b runs tasks [seg[b], seg[b + 1]) one after another, so
+// tasks that add into the same output are summed in a fixed order by one
+// block (no two blocks write one output).
+__global__ void reduce_seg_kernel(const ReduceTask* tasks, const int* seg) {
+    __shared__ double sh[256];
+    for (int k = seg[blockIdx.x]; k < seg[blockIdx.x + 1]; ++k) {
+        const ReduceTask t = tasks[k];
+        for (int s = 0; s < t.count; ++s) {
+            double acc = 0.0;
+            for (int64_t i = threadIdx.x; i < t.ntiles; i += blockDim.x) acc += t.partials[i * t.np + t.off + s];
+            sh[threadIdx.x] = acc;
+            __syncthreads();
+            for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+                if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                if (t.accumulate) t.out[s] += t.mult * sh[0];
+                else t.out[s] = t.mult * sh[0];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_reduce_seg(const ReduceTask* tasks, const int* seg, int nseg, cudaStream_t st) {
+    if (nseg <= 0) return cudaSuccess;
+    reduce_seg_kernel<<<nseg, 256, 0, st>>>(tasks, seg);
+    return note_launch(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // Full enumeration (the t_FE ground-state search of Table III): every thread
 // evaluates 64 consecutive basis states (register bits = qubits 0..5) with

@@ -124,6 +124,36 @@ QS_PHD constexpr PairAdjLayout pair_adj_layout(int C) {
     return t;
 }
 
+// Forward layouts of the run-structured shape A (kind 0 with runs: tile bits
+// [0, 8) one 2 KB run, [8, 12) the top four qubits, 12 the batch bit; targets
+// [0, 12)).  The pack bit is tile bit 0 (a pair is two adjacent amplitudes,
+// one 16-byte unit).  Layout 0 holds five run bits in the registers and puts
+// run bits 1..5 on the lanes, so its stores are 512 contiguous bytes per warp;
+// layout 1 holds run bits 1..5 and has tile bit 11 on lane bit 0, rotated by
+// lane shuffles (two layouts of five bits plus the pack bit hold eleven of the
+// twelve targets).
+struct PairRunsLayout {
+    int regs[2][5];
+    int tbits[2][7];
+    int shuf;  // tile bit on lane bit 0 of layout 1, rotated by shuffles
+};
+
+QS_PHD constexpr PairRunsLayout pair_runs_layout() {
+    PairRunsLayout t{};
+    const int r0[5] = {6, 7, 8, 9, 10}, t0[7] = {1, 2, 3, 4, 5, 11, 12};
+    const int r1[5] = {1, 2, 3, 4, 5}, t1[7] = {11, 6, 7, 8, 9, 10, 12};
+    for (int b = 0; b < 5; ++b) {
+        t.regs[0][b] = r0[b];
+        t.regs[1][b] = r1[b];
+    }
+    for (int i = 0; i < 7; ++i) {
+        t.tbits[0][i] = t0[i];
+        t.tbits[1][i] = t1[i];
+    }
+    t.shuf = 11;
+    return t;
+}
+
 // Pair unit of tile element e: e with the pack bit P removed.
 QS_PHD constexpr unsigned pair_unit(unsigned e, int P) {
     return (e & ((1u << P) - 1u)) | ((e >> (P + 1)) << P);

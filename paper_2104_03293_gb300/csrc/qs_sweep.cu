@@ -17,6 +17,7 @@ cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st) {
     const int64_t groups = L.total_tiles / (L.group > 0 ? L.group : 1);
     if (grid > groups) grid = (int)groups;
     if (grid < 1) grid = 1;
+    if (L.pairc == 1 && !L.adjoint) return launch_sweep_runs(L, grid, st);
     if (L.pairc) return L.adjoint ? launch_sweep_pair_adj(L, grid, st) : launch_sweep_pair(L, grid, st);
     cudaError_t s = cudaErrorInvalidValue;
     if (!L.adjoint && (L.variant == V_ZFULL || L.variant == V_ZPHASE)) sweep_zexp(L.dtype, L.kind, false, &L, grid, st, &s);
@@ -32,7 +33,8 @@ int sweep_grid(int dtype, int adjoint, int kind) {
 
 int pair_choice(int dtype, int adjoint, int kind, int c, int variant) {
     if (dtype != 0) return 0;
-    if (kind == 0) return (adjoint && c == kRunBits) ? 1 : 0;  // run-structured shape A (adjoint)
+    if (kind == 0)  // run-structured shape A
+        return (c == kRunBits && (adjoint || variant == V_PHASE || variant == V_LEAN)) ? 1 : 0;
     if (kind != 1 || !(c == 2 || c == 3)) return 0;
     return (adjoint || variant == V_PHASE || variant == V_LEAN || variant == V_ZPHASE) ? c : 0;
 }

@@ -288,9 +288,13 @@ struct SlotCost {
             for (int k = 0; k < (1 << b2); ++k) phi[k | (1 << b2)] = phi[k] - 2 * fb[R1 + b2];
     }
     __device__ __forceinline__ int idx(int m) const { return plo[m & ((1 << R1) - 1)] + phi[m >> R1] + __ldg(q + m); }
+    // without the intra-register couplings Q[m] (the caller adds them)
+    __device__ __forceinline__ int idx_noq(int m) const { return plo[m & ((1 << R1) - 1)] + phi[m >> R1]; }
     // table index, kept inside [0, top] so that no cost can address memory
-    // outside the phase table
-    __device__ __forceinline__ int tidx(int m, int top) const { return min(max(idx(m), 0), top); }
+    // outside the phase table (one unsigned minimum: a negative index wraps
+    // to a large one and is clamped to top)
+    __device__ __forceinline__ static int clamp_tab(int ix, int top) { return (int)min((unsigned)ix, (unsigned)top); }
+    __device__ __forceinline__ int tidx(int m, int top) const { return clamp_tab(idx(m), top); }
 };
 
 // Warp-level sum, lane 0 stores into red[warp * nslots + slot].

@@ -161,17 +161,22 @@ struct PairSweep {
     }
 
     // ---- phase: slot m = lane | j << 1 (cost program of the layout) ------------
+    // Q[m] comes from the kernel parameters; the layer's table (a generic
+    // pointer) lies in shared memory when it was staged at kernel start, else
+    // in global memory.
     template <int g>
     __device__ static __forceinline__ void phase(float2 (&X)[NJ], float2 (&Y)[NJ], const SweepTask& T,
                                                  const TileTab& tt, uint32_t tid, const float2* __restrict__ tab,
-                                                 int frame) {
+                                                 int frame, const PairQ& pq) {
         SlotCost<6> sc;
         sc.template init_tile<Map<g>, 7>(tt, T.cprog[g], tid, frame, T.cost_lo);
         const int top = T.tab_stride - 1;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const float2 fa = __ldg(tab + sc.tidx(2 * j, top));
-            const float2 fb = __ldg(tab + sc.tidx(2 * j + 1, top));
+            const int ia = SlotCost<6>::clamp_tab(sc.idx_noq(2 * j) + pq.q[g][2 * j], top);
+            const int ib = SlotCost<6>::clamp_tab(sc.idx_noq(2 * j + 1) + pq.q[g][2 * j + 1], top);
+            const float2 fa = tab[ia];
+            const float2 fb = tab[ib];
             const float ar = X[j].x, br = X[j].y, ai = Y[j].x, bi = Y[j].y;
             X[j] = make_float2(fmaf(ar, fa.x, -ai * fa.y), fmaf(br, fb.x, -bi * fb.y));
             Y[j] = make_float2(fmaf(ar, fa.y, ai * fa.x), fmaf(br, fb.y, bi * fb.x));
@@ -197,18 +202,23 @@ __device__ __forceinline__ void cluster_sync_all() {
 // barrier once per tile, also after a timed-out wait.
 template <int V> struct PairOcc { static constexpr int value = 3; };  // CTAs per SM (every variant)
 
+// V_PHASE stages the layer table of its phase in shared memory when it has at
+// most this many entries (the three CTAs of an SM still fit).
+constexpr int kPairTabSmem = 1024;
+
 template <int C, int V, int CL>
 __global__ void __launch_bounds__(128, PairOcc<V>::value)
     sweep_pair_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
-                      int64_t total, int* __restrict__ err) {
+                      int64_t total, int* __restrict__ err, const __grid_constant__ PairQ pq) {
     using S = PairSweep<C>;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NB = S::NB;
-    constexpr bool kPhase = V != V_LEAN, kZ = V == V_ZPHASE;
+    constexpr bool kPhase = V != V_LEAN, kZ = V == V_ZPHASE, kSTab = V == V_PHASE;
     extern __shared__ __align__(128) unsigned char smraw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     double* zacc = reinterpret_cast<double*>(smraw + S::SMEM_BYTES);  // kZ: [kZSlots][kZQ]
     float* zred = reinterpret_cast<float*>(smraw + S::SMEM_BYTES + (size_t)kZSlots * kZQ * 8);
+    float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // kSTab: [kPairTabSmem]
     const uint32_t tid = threadIdx.x;
     const bool zon = kZ && (tasks[0].flags & T_ZEXP);  // one task per launch
     uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
@@ -251,6 +261,20 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     }
     if (zon)
         for (int i = (int)tid; i < kZSlots * kZQ; i += NT) zacc[i] = 0.0;
+    // the table of the (first) layer whose phase this sweep applies
+    int slayer = -1;
+    if (kSTab && ntasks == 1 && tasks[0].tab_stride <= kPairTabSmem) {
+        const SweepTask& T0 = tasks[0];
+        for (int r = 0; r < T0.nrounds; ++r)
+            if (T0.rounds[r].phase_pre) {
+                slayer = T0.rounds[r].layer;
+                break;
+            }
+        if (slayer >= 0) {
+            const float2* src = reinterpret_cast<const float2*>(T0.tab) + (int64_t)slayer * T0.tab_stride;
+            for (int i = (int)tid; i < T0.tab_stride; i += NT) stab[i] = __ldg(src + i);
+        }
+    }
     __syncthreads();
     for (int b = 0; b < NB; ++b) {
         const int64_t g0 = (int64_t)blockIdx.x + (int64_t)b * gridDim.x;
@@ -315,9 +339,10 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             cur = g;
             if (++done_tr == ntr) release();
         };
-        auto do_phase = [&](const float2* ltab, int frame) {
-            if (cur == 0) S::template phase<0>(X, Y, T, tt, tid, ltab, frame);
-            else S::template phase<1>(X, Y, T, tt, tid, ltab, frame);
+        auto do_phase = [&](const float2* ltab, int frame, bool staged) {
+            const float2* t = (kSTab && staged) ? stab : ltab;
+            if (cur == 0) S::template phase<0>(X, Y, T, tt, tid, t, frame, pq);
+            else S::template phase<1>(X, Y, T, tt, tid, t, frame, pq);
         };
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {
@@ -331,7 +356,7 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
                 if (cur == 0) S::template zexp<0>(X, Y, tid, zred, za, tm, base, T.n, sg);
                 else S::template zexp<1>(X, Y, tid, zred, za, tm, base, T.n, sg);
             }
-            if (kPhase && rd.phase_pre) do_phase(ltab, ly.frame);
+            if (kPhase && rd.phase_pre) do_phase(ltab, ly.frame, rd.layer == slayer);
             const float w = (float)ly.w;
             // zig-zag: a round starts in the current layout
             if (cur == 0) {
@@ -343,7 +368,7 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
                 to_layout(0);
                 S::template rotate<0>(X, Y, w);
             }
-            if (kPhase && rd.phase_post) do_phase(ltab, ly.frame);
+            if (kPhase && rd.phase_post) do_phase(ltab, ly.frame, rd.layer == slayer);
         }
         to_layout(0);
 
@@ -390,11 +415,16 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
 }
 
 template <int C, int V>
-constexpr size_t pair_smem() { return PairSweep<C>::SMEM_BYTES + (V == V_ZPHASE ? PairSweep<C>::Z_BYTES : 0); }
+constexpr size_t pair_smem() {
+    return PairSweep<C>::SMEM_BYTES + (V == V_ZPHASE ? PairSweep<C>::Z_BYTES : 0) +
+           (V == V_PHASE ? (size_t)kPairTabSmem * sizeof(float2) : 0);
+}
 
 template <int C, int V>
 static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
     constexpr size_t smem = pair_smem<C, V>();
+    if (V != V_LEAN && !L.pq) return cudaErrorInvalidValue;  // the phase needs the Q tables
+    const PairQ pq = L.pq ? *L.pq : PairQ{};
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -419,11 +449,11 @@ static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t 
         cfg.attrs = at;
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, sweep_pair_kernel<C, V, 4>, L.tasks, L.tile_prefix, L.ntasks,
-                                           L.total_tiles, L.err);
+                                           L.total_tiles, L.err, pq);
         return note_launch(e);
     }
     sweep_pair_kernel<C, V, 1><<<grid, PairSweep<C>::NT, smem, st>>>(L.tasks, L.tile_prefix, L.ntasks,
-                                                                      L.total_tiles, L.err);
+                                                                      L.total_tiles, L.err, pq);
     return note_launch(cudaGetLastError());
 }
 

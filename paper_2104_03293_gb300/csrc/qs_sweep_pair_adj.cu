@@ -207,20 +207,23 @@ struct PairAdj {
     }
 
     // phase of the layer on both arrays, then the dF/dgamma term C Im(conj(l) p)
-    // (slot m = half | j << 1 of the layout's cost program)
+    // (slot m = half | j << 1 of the layout's cost program; Q[m] from the
+    // kernel parameters; the table through a generic pointer, in shared
+    // memory when it was staged at kernel start)
     template <int g>
     __device__ static __forceinline__ void phase(float2 (&Xp)[NJ], float2 (&Yp)[NJ], float2 (&Xl)[NJ],
                                                  float2 (&Yl)[NJ], const SweepTask& T, const TileTab& tt,
                                                  uint32_t tid, const float2* __restrict__ tab, int frame,
-                                                 float& gacc) {
+                                                 float& gacc, const PairAdjQ& pq) {
         SlotCost<5> sc;
         sc.template init_tile<Map<g>, 8>(tt, T.cprog[g], tid, frame, T.cost_lo);
         const int top = T.tab_stride - 1;
         float part = 0.f;
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const int ia = sc.tidx(2 * j, top), ib = sc.tidx(2 * j + 1, top);
-            const float2 fa = __ldg(tab + ia), fb = __ldg(tab + ib);
+            const int ia = SlotCost<5>::clamp_tab(sc.idx_noq(2 * j) + pq.q[g][2 * j], top);
+            const int ib = SlotCost<5>::clamp_tab(sc.idx_noq(2 * j + 1) + pq.q[g][2 * j + 1], top);
+            const float2 fa = tab[ia], fb = tab[ib];
             const float par = Xp[j].x, pbr = Xp[j].y, pai = Yp[j].x, pbi = Yp[j].y;
             const float lar = Xl[j].x, lbr = Xl[j].y, lai = Yl[j].x, lbi = Yl[j].y;
             const float npar = fmaf(par, fa.x, -pai * fa.y), npai = fmaf(par, fa.y, pai * fa.x);
@@ -240,10 +243,14 @@ struct PairAdj {
 
 }  // namespace
 
+// The un-phase of a reverse sweep reads its layer table from shared memory
+// when it has at most this many entries.
+constexpr int kAdjTabSmem = 1024;
+
 template <int C>
 __global__ void __launch_bounds__(256, 1)
     sweep_pair_adj_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
-                          int64_t total, int* __restrict__ err) {
+                          int64_t total, int* __restrict__ err, const __grid_constant__ PairAdjQ pq) {
     using S = PairAdj<C>;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NW = S::NW, NSLOT = S::NSLOT;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -252,6 +259,7 @@ __global__ void __launch_bounds__(256, 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + 3 * S::TILE_BYTES);
     double* red = reinterpret_cast<double*>(smraw + 3 * S::TILE_BYTES + 64);
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
+    float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // [kAdjTabSmem]
     const uint32_t tid = threadIdx.x;
     uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
     float2 Xp[NJ], Yp[NJ], Xl[NJ], Yl[NJ];
@@ -292,6 +300,20 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0) {
         mbar_init(full, NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the table of the (first) layer whose phase this sweep un-applies
+    int slayer = -1;
+    if (ntasks == 1 && tasks[0].tab_stride <= kAdjTabSmem) {
+        const SweepTask& T0 = tasks[0];
+        for (int r = 0; r < T0.nrounds; ++r)
+            if (T0.rounds[r].phase_pre || T0.rounds[r].phase_post) {
+                slayer = T0.rounds[r].layer;
+                break;
+            }
+        if (slayer >= 0) {
+            const float2* src = reinterpret_cast<const float2*>(T0.tab) + (int64_t)slayer * T0.tab_stride;
+            for (int i = (int)tid; i < T0.tab_stride; i += NT) stab[i] = __ldg(src + i);
+        }
     }
     __syncthreads();
     if ((int64_t)blockIdx.x < total) issue(blockIdx.x);
@@ -348,10 +370,11 @@ __global__ void __launch_bounds__(256, 1)
             else if (cur == 1) S::template rotate<1>(Xp, Yp, Xl, Yl, w, fabs2, fpow, gB);
             else S::template rotate<2>(Xp, Yp, Xl, Yl, w, fabs2, fpow, gB);
         };
-        auto do_phase = [&](const float2* ltab, int frame, float& gG) {
-            if (cur == 0) S::template phase<0>(Xp, Yp, Xl, Yl, T, tt, tid, ltab, frame, gG);
-            else if (cur == 1) S::template phase<1>(Xp, Yp, Xl, Yl, T, tt, tid, ltab, frame, gG);
-            else S::template phase<2>(Xp, Yp, Xl, Yl, T, tt, tid, ltab, frame, gG);
+        auto do_phase = [&](const float2* ltab, int frame, float& gG, bool staged) {
+            const float2* t = staged ? stab : ltab;
+            if (cur == 0) S::template phase<0>(Xp, Yp, Xl, Yl, T, tt, tid, t, frame, gG, pq);
+            else if (cur == 1) S::template phase<1>(Xp, Yp, Xl, Yl, T, tt, tid, t, frame, gG, pq);
+            else S::template phase<2>(Xp, Yp, Xl, Yl, T, tt, tid, t, frame, gG, pq);
         };
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {
@@ -359,7 +382,7 @@ __global__ void __launch_bounds__(256, 1)
             const LayerDev ly = T.layers[rd.layer];
             const float2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
             float gB = 0.f, gG = 0.f;
-            if (rd.phase_pre) do_phase(ltab, ly.frame, gG);
+            if (rd.phase_pre) do_phase(ltab, ly.frame, gG, rd.layer == slayer);
             const float fabs2 = (float)(ly.fabs * ly.fabs);
             float fpow = 1.f;
             for (int i = 0; i < rd.r0; ++i) fpow *= fabs2;  // |f|^{2 r0}
@@ -378,7 +401,7 @@ __global__ void __launch_bounds__(256, 1)
                 to_layout(0);
                 rotate_cur(w, fabs2, fpow, gB);
             }
-            if (rd.phase_post) do_phase(ltab, ly.frame, gG);
+            if (rd.phase_post) do_phase(ltab, ly.frame, gG, rd.layer == slayer);
             warp_sum_f(gB, red, 2 * r, NSLOT);
             warp_sum_f(gG, red, 2 * r + 1, NSLOT);
         }
@@ -407,16 +430,20 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 template <int C>
+constexpr size_t pair_adj_smem() { return PairAdj<C>::SMEM_BYTES + (size_t)kAdjTabSmem * sizeof(float2); }
+
+template <int C>
 static cudaError_t launch_pair_adj_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(sweep_pair_adj_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)PairAdj<C>::SMEM_BYTES);
+                                             (int)pair_adj_smem<C>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    sweep_pair_adj_kernel<C><<<grid, PairAdj<C>::NT, PairAdj<C>::SMEM_BYTES, st>>>(L.tasks, L.tile_prefix, L.ntasks,
-                                                                                    L.total_tiles, L.err);
+    if (!L.paq) return cudaErrorInvalidValue;  // the un-phase needs the Q tables
+    sweep_pair_adj_kernel<C><<<grid, PairAdj<C>::NT, pair_adj_smem<C>(), st>>>(L.tasks, L.tile_prefix, L.ntasks,
+                                                                                L.total_tiles, L.err, *L.paq);
     return note_launch(cudaGetLastError());
 }
 
@@ -429,12 +456,12 @@ cudaError_t launch_sweep_pair_adj(const SweepLaunch& L, int grid, cudaStream_t s
 
 int sweep_pair_adj_grid() {
     cudaFuncSetAttribute(sweep_pair_adj_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)PairAdj<2>::SMEM_BYTES);
+                         (int)pair_adj_smem<2>());
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_adj_kernel<2>, PairAdj<2>::NT,
-                                                  PairAdj<2>::SMEM_BYTES);
+                                                  pair_adj_smem<2>());
     if (per_sm < 1) per_sm = 1;
     return per_sm * sms;
 }

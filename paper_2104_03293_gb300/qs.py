@@ -80,6 +80,7 @@ _SIGS = {
     "qs_batch_grad": [_P, _I, _PD, _PD, _PD],
     "qs_batch_adam": [_P, _I, _D, _D, _D, _D, _PD, _PD, _I],
     "qs_batch_destroy": [_P],
+    "qs_batch_test_withhold": [_P, _I, _D],
     "qs_batch_partition": [_I, _PI, _PI, _I, _PI, _PD],
 }
 
@@ -420,6 +421,12 @@ class Batch:
         dg, db = np.zeros(max(tot, 1)), np.zeros(max(tot, 1))
         _check(lib().qs_batch_grad(self._h, int(objective), _dptr(v), _dptr(dg), _dptr(db)))
         return v, self._split(dg), self._split(db)
+
+    def test_withhold(self, idx: int, wait_limit_s: float):
+        """Failure-detection test: the next evolve withholds one dependency of
+        instance idx and gives up after wait_limit_s (results then raise
+        QS_ETIMEOUT; the batch stays usable)."""
+        _check(lib().qs_batch_test_withhold(self._h, int(idx), float(wait_limit_s)))
 
     def adam(self, gammas, betas, steps: int, lr=0.01, b1=0.9, b2=0.999, eps=1e-8, use_graph: bool = True):
         if self.p is None:

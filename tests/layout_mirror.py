@@ -167,6 +167,13 @@ def pair_adj_layout(C):
                 rotmask=[0xf, 0xf, 0x1])
 
 
+def pair_runs_layout():
+    """Forward layouts of the run-structured shape A (pack bit = tile bit 0;
+    tile bit 11 on lane bit 0 of layout 1, rotated by shuffles)."""
+    return dict(P=0, regs=[[6, 7, 8, 9, 10], [1, 2, 3, 4, 5]],
+                tbits=[[1, 2, 3, 4, 5, 11, 12], [11, 6, 7, 8, 9, 10, 12]], shuf=11)
+
+
 def land(e, P):
     """Landing-buffer position of tile element e (packed-pair adjoint)."""
     return e if P == 0 else e ^ (((e >> 4) & 1) << P)

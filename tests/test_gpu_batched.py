@@ -193,3 +193,26 @@ def test_config4_full_batch_adam_against_oracle(qs):
         assert_readout(insts[i], E[i], P[i], Er, Pr, i)
     # 200 steps of minimisation lower the energy of every sampled instance
     assert np.all(E[idx] < E0), (E[idx], E0)
+
+
+def test_queue_withheld_dependency_times_out(qs):
+    """Failure detection without a GPU fault: a work queue whose instance 1
+    waits for one tile that no sweep provides gives up after its 50 ms limit;
+    the error reaches the host as QS_ETIMEOUT, no copy is left in flight, and
+    the next evolve of the same batch is correct again."""
+    insts = [I.erdos_renyi_ising(n, I.workload_seed(2, 900 + n)) for n in (16, 18, 20)]
+    gs, bs = zip(*[I.uniform_angles(3, I.workload_seed(2, 950 + k)) for k in range(3)])
+    bt = _batch(qs, insts)
+    try:
+        bt.test_withhold(1, 0.05)
+        bt.evolve(list(gs), list(bs))
+        with pytest.raises(qs.QSError) as exc:
+            bt.results()
+        assert exc.value.code == qs.QS_ETIMEOUT
+        bt.evolve(list(gs), list(bs))
+        E, P = bt.results()
+    finally:
+        bt.close()
+    for i, inst in enumerate(insts):
+        Er, Pr, _ = oracle.readout(inst, oracle.evolve(inst, gs[i], bs[i]))
+        assert_readout(inst, E[i], P[i], Er, Pr, i)

@@ -12,7 +12,7 @@ the GPU as an out-of-bounds access.
 import numpy as np
 import pytest
 
-from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_adj_layout, pair_layout,
+from layout_mirror import (CFG, FAR_BIT_C64, MIN_PHYS, PAGE_BIT, PAIR_K, e_slot, e_thread, make_layout, make_shapes, pair_adj_layout, pair_layout, pair_runs_layout,
                            land, land_fwd, pair_phys, pair_unit, phys, rank_of, slot_off0, tile_base, tile_to_global)
 
 
@@ -131,6 +131,41 @@ def test_pair_layouts(C):
             if sh["c"] + sh["n1"] <= 8:
                 shift = sh["g1"] + 8 - sh["c"] - sh["n1"]
                 assert all(tile_to_global(j << 8, sh) == j << shift for j in range(32))
+
+
+def test_pair_runs_layouts():
+    """Run-structured shape A, forward packed pairs: (thread, pair, half)
+    covers the tile once in both layouts; the targets [0, 12) are rotated
+    once per round (pack bit and registers of layout 0, registers of layout
+    1, the shuffle bit on lane bit 0 of layout 1), the batch bit 12 never;
+    the 16-byte transposes are conflict-free per quarter-warp; the landing
+    reads into layout 0 are 512 contiguous bytes per warp; the store offsets
+    of layout 0's slots are (j & 3) << 6 plus (j >> 2) << g0."""
+    L = pair_runs_layout()
+    P = L["P"]
+    for g in range(2):
+        regs, tb = L["regs"][g], L["tbits"][g]
+        assert sorted(regs + tb + [P]) == list(range(PAIR_K))
+        es = [sum(((j >> b) & 1) << regs[b] for b in range(5)) for j in range(32)]
+        et = [sum(((t >> i) & 1) << tb[i] for i in range(7)) for t in range(128)]
+        assert len({a | s | (h << P) for a in et for s in es for h in range(2)}) == 1 << PAIR_K
+        for j in range(32):
+            for w0 in range(0, 128, 32):
+                for q in range(0, 32, 8):
+                    banks = {pair_phys(pair_unit(et[w0 + q + l] | es[j], P)) % 8 for l in range(8)}
+                    assert len(banks) == 8, (g, j, w0, q)
+                if g == 0:
+                    units = sorted((et[w0 + l] | es[j]) >> 1 for l in range(32))
+                    assert units == list(range(units[0], units[0] + 32))
+    assert L["tbits"][1][0] == L["shuf"]
+    rotated = [P] + L["regs"][0] + L["regs"][1] + [L["shuf"]]
+    assert sorted(rotated) == list(range(12))
+    for n in (33, 34):
+        sh = make_shapes(n, 13, 13, 2, PAGE_BIT["c64"])[0]
+        assert sh["c"] == 8 and sh["n1"] == 4 and sh["g0"] == n - 4
+        for j in range(32):
+            e = sum(((j >> b) & 1) << L["regs"][0][b] for b in range(5))
+            assert tile_to_global(e, sh) == ((j & 3) << 6) + ((j >> 2) << sh["g0"])
 
 
 @pytest.mark.parametrize("C", [1, 2, 3])
