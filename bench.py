@@ -197,6 +197,7 @@ def secondary_workloads(qs, I, torch):
     items = I.config2()
     insts = [it[0] for it in items]
     gs, bs = [it[1] for it in items], [it[2] for it in items]
+    insts512, gs512, bs512 = insts, gs, bs
     bt = qs.Batch([x.n for x in insts])
     for i, x in enumerate(insts):
         bt.set_ising(i, x.h, x.edges, x.J)
@@ -258,6 +259,33 @@ def secondary_workloads(qs, I, torch):
     t_adam = 1e3 * (time.perf_counter() - t0)
     bt.close()
     out["adam_64x200"] = {"ms": t_adam, "mean_E": float(np.mean(E)), "mean_P_ground": float(np.mean(P))}
+    # plan autotuner at n = 24 and 30: every candidate re-timed over 8 layers
+    # against the kept rule
+    for nt in (24, 30):
+        x = I.erdos_renyi_ising(nt, I.workload_seed(5, 300 + nt), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+        gg, bb = qs.aqa_angles(0.75, np.arange(1, 9) / 9.0)
+        st = qs.State(nt)
+        st.set_ising(x.h, x.edges, x.J)
+        kept, _, cands = st.autotune_plan(2)
+        full = {}
+        for r, _ in cands:
+            st.set_plan_rule(r)
+            full[tuple(r)] = timed(lambda: st.evolve(gg, bb), 3)
+        st.close()
+        best = min(full.values())
+        out[f"autotune_n{nt}"] = {"kept": list(kept), "kept_ms_p8": full[tuple(kept)], "best_ms_p8": best,
+                                  "kept_over_best": full[tuple(kept)] / best,
+                                  "candidates_ms_p8": [[list(r), m] for r, m in full.items()]}
+    # batched queue: launch rules timed on the 512-instance forward
+    bt = qs.Batch([x.n for x in insts512])
+    for i, x in enumerate(insts512):
+        bt.set_ising(i, x.h, x.edges, x.J)
+    bt.evolve(gs512, bs512)
+    c, w, ms = bt.autotune()
+    t_tuned = timed(lambda: (bt.evolve(gs512, bs512), bt.results()), 3)
+    bt.close()
+    out["batched_512"].update({"autotuned_rule": [c, w], "autotuned_ms": t_tuned,
+                               "autotuned_speedup_vs_tiled": out["batched_512"]["one_at_a_time_tiled_ms"] / t_tuned})
     # p = 1 landscape: 64 x 64 (gamma, beta) grid of one n = 18 instance
     inst = I.erdos_renyi_ising(18, I.workload_seed(6, 2), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
     gam = np.arange(64) * (2 * np.pi / 64)
@@ -356,8 +384,15 @@ def main():
         st2.set_adjoint_buffer(half[1])
     else:
         st2 = qs.State(n2, "c64")
-    _, sweeps = qs.plan_sweeps(n, p)
-    _, sweeps2 = qs.plan_sweeps(n2, p)
+    # plan rules from the autotuner (outside the timed region; a JSON cache in
+    # QS_TUNE_CACHE makes later runs skip the search)
+    tune_cache = os.environ.get("QS_TUNE_CACHE")
+    st.set_ising(inst.h, inst.edges, inst.J)
+    rule, rule_ms, cands = st.autotune_plan(2, cache=tune_cache)
+    st2.set_ising(inst2.h, inst2.edges, inst2.J)
+    rule2, rule2_ms, cands2 = st2.autotune_plan(2, cache=tune_cache)
+    _, sweeps = st.plan_info(p)
+    _, sweeps2 = st2.plan_info(p)
     stream = torch.cuda.current_stream()
 
     def step(timing):
@@ -425,6 +460,30 @@ def main():
     e2e_s = statistics.mean(timing["e2e_s"])
     h2d = inst.h.nbytes + inst.edges.nbytes + inst.J.nbytes + 2 * 8 * p
     d2h = 3 * 8
+    # the tuned plan against the runner-up candidate, both over the full p
+    # layers (after the timed region)
+    tuned = {"n": n, "rule": list(rule), "trial_ms": rule_ms,
+             "candidates": [[list(r), m] for r, m in cands], "n2": n2, "rule2": list(rule2),
+             "candidates2": [[list(r), m] for r, m in cands2]}
+    others = sorted((m, r) for r, m in cands if tuple(r) != tuple(rule))
+    if others:
+        g, b = qs.aqa_angles(tau, s)
+        def full_ms(r):
+            st.set_plan_rule(r)
+            st.set_ising(inst.h, inst.edges, inst.J)
+            st.evolve(g, b)
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            st.evolve(g, b)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            return t0.elapsed_time(t1)
+        runner = others[0][1]
+        ms_run = full_ms(runner)
+        ms_kept = full_ms(rule)
+        tuned.update({"runner_up": list(runner), "kept_p_ms": ms_kept, "runner_up_p_ms": ms_run,
+                      "kept_over_best": ms_kept / min(ms_kept, ms_run)})
     # per-layer <Z_i> recorded inside the same evolve (after the timed region)
     g, b = qs.aqa_angles(tau, s)
     st.set_ising(inst.h, inst.edges, inst.J)
@@ -451,7 +510,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": dict(workload_config(args), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "config": dict(workload_config(args), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       plan_rule=list(rule), plan_rule_grad=list(rule2)),
         "layer_ms": evolve_ms / p,
         "sweeps_per_evolve": sweeps,
         "grad_forward_equivalents": grad_fe,
@@ -468,6 +528,7 @@ def main():
         "clocks": clk,
         "readout": {"E": E, "P_ground": P, "grad_P": v, "dP_dtau": dtau},
         "zexp": zexp,
+        "autotune": tuned,
         "secondary": extra,
     }
     print(json.dumps(line), flush=True)

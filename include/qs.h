@@ -186,10 +186,36 @@ int qs_enumerate_noalloc(int n, const double* hfield, int n_edges, const int32_t
  * Errors: QS_EINVAL. */
 int qs_set_shape_rule(qs_handle h, int runs_a, int split);
 
-/* Autotuner: time p_trial layers (from |+>, fixed angles) under each
- * candidate shape plan on this GPU and keep the fastest; reports it (any
- * pointer may be NULL).  Overwrites the state.  Call after qs_set_ising.
- * Errors: QS_ESTATE, QS_EINVAL, QS_ECUDA. */
+/* Plan rule of the handle: five ints
+ *   [0] runs_a, [1] split   as qs_set_shape_rule;
+ *   [2] cmin         carried low bits of the strided shapes: 2 (rows of 32
+ *                    bytes, 11 targets per shape) or 3 (64-byte rows, 10
+ *                    targets; more shapes); -1 the default (2);
+ *   [3] ctas_per_sm  persistent CTAs per SM of the sweep kernels (0: as many
+ *                    as fit);
+ *   [4] pair_cluster 4: the strided packed-pair sweeps run in 4-CTA
+ *                    clusters that fetch shared HBM lines once; 1: without.
+ * Every rule gives the same results up to rounding order.  qs_set_plan_rule
+ * re-plans the current Ising cost when the shape fields change.  Errors:
+ * QS_EINVAL. */
+int qs_set_plan_rule(qs_handle h, const int* rule);
+int qs_get_plan_rule(qs_handle h, int* rule);
+
+/* Autotuner: times p_trial layers (from |+>, fixed angles; one warm-up, the
+ * faster of two runs) under candidate plan rules on this GPU and keeps the
+ * fastest.  Search, coordinate by coordinate: tile shapes first (contiguous
+ * shape A; for complex64 states of 24 qubits and more the run-structured A
+ * with split bits 20, 22 and 24; each with cmin 2 and 3), then, for the best
+ * shapes, one CTA per SM fewer than fit and (complex64) the strided sweeps
+ * without clusters.  Reports the measured candidates (up to max_cand rules
+ * of five ints in cand_rules with their times in cand_ms, the count in
+ * ncand) and the kept rule (best_rule, five ints) with its time; any output
+ * may be NULL when max_cand = 0.  Overwrites the state.  Call after
+ * qs_set_ising.  Errors: QS_ESTATE, QS_EINVAL, QS_ECUDA. */
+int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand_rules, double* cand_ms,
+                   int* best_rule, double* best_ms);
+
+/* qs_autotune_ex reporting only runs_a, split and the time. */
 int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_ms);
 
 /* Gradient of F = <psi_p|O|psi_p> with respect to all 2p angles, where O is
@@ -323,6 +349,22 @@ int qs_batch_grad(qs_batch_handle b, int objective, double* value, double* dgamm
  * qs_batch_results gives E and P_ground at the final angles.  Synchronises. */
 int qs_batch_adam(qs_batch_handle b, int steps, double lr, double b1, double b2, double eps,
                   double* gamma_io, double* beta_io, int use_graph);
+
+/* Launch rule of the batch's work queue: ctas_per_sm persistent CTAs per SM
+ * (0: as many as fit); window_bytes > 0 orders the queue in windows of
+ * consecutive instances holding at most that many state bytes (wave by wave
+ * inside a window, so its states can stay in L2 between sweeps); 0: one
+ * window of every instance.  Same results up to rounding order.  Errors:
+ * QS_EINVAL. */
+int qs_batch_set_launch_rule(qs_batch_handle b, int ctas_per_sm, int64_t window_bytes);
+
+/* Batch autotuner: times the batch's forward at the angles of the last
+ * qs_batch_evolve (one warm-up, the faster of two runs) for ctas_per_sm in
+ * {as many as fit, one fewer} and window_bytes in {one window, 256 MiB,
+ * 64 MiB}, keeps the fastest and reports it (any pointer may be NULL).
+ * Overwrites the states; qs_batch_results needs a new evolve.  Errors:
+ * QS_ESTATE, QS_ECUDA, QS_ETIMEOUT. */
+int qs_batch_autotune(qs_batch_handle b, int* ctas_per_sm, int64_t* window_bytes, double* best_ms);
 
 /* Failure-detection test hook (no counterpart in the paper).  Arms the next
  * qs_batch_evolve to run a work queue in which the second sweep of instance

@@ -228,6 +228,9 @@ struct qs_state {
     bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
     int device = 0;
     ShapeRule rule;                      // tile-shape plan (qs_set_shape_rule / qs_autotune)
+    int ctas_per_sm = 0;                 // launch rule: persistent CTAs per SM (0 = as many as fit)
+    int pair_cluster = 4;                // launch rule: strided packed-pair sweeps in 4-CTA clusters or not
+    int sms = 0;                         // multiprocessors of the device
     std::vector<double> ising_h, ising_J;  // the last qs_set_ising input, to re-plan
     std::vector<int32_t> ising_e;
 };
@@ -271,6 +274,8 @@ static int check_device_error(qs_handle h) {
     }
     return QS_OK;
 }
+
+static int grid_for(qs_handle h, int kind, int adjoint);
 
 extern "C" {
 
@@ -358,49 +363,147 @@ int qs_set_shape_rule(qs_handle h, int runs_a, int split) {
     if (int rc = check_handle(h)) return rc;
     if (runs_a < -1 || runs_a > 1 || split < -1 || split >= h->nphys + 1)
         return set_error(QS_EINVAL, "qs_set_shape_rule: runs_a in {-1, 0, 1}, split in [-1, n]");
-    h->rule = ShapeRule{runs_a, split};
+    h->rule = ShapeRule{runs_a, split, h->rule.cmin};
     return replan(h);
 }
 
-int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_ms) {
+int qs_set_plan_rule(qs_handle h, const int* rule) {
+    if (int rc = check_handle(h)) return rc;
+    if (!rule) return set_error(QS_EINVAL, "qs_set_plan_rule: rule is NULL");
+    const int runs_a = rule[0], split = rule[1], cmin = rule[2], cps = rule[3], cl = rule[4];
+    if (runs_a < -1 || runs_a > 1 || split < -1 || split >= h->nphys + 1 || !(cmin == -1 || cmin == 2 || cmin == 3) ||
+        cps < 0 || cps > 32 || !(cl == 1 || cl == 4))
+        return set_error(QS_EINVAL, "qs_set_plan_rule: runs_a in {-1, 0, 1}, split in [-1, n], cmin in {-1, 2, 3}, "
+                                    "ctas_per_sm in [0, 32], pair_cluster in {1, 4}");
+    const bool reshape = runs_a != h->rule.runs_a || split != h->rule.split || cmin != h->rule.cmin;
+    h->rule = ShapeRule{runs_a, split, cmin};
+    h->ctas_per_sm = cps;
+    h->pair_cluster = cl;
+    return reshape ? replan(h) : QS_OK;
+}
+
+int qs_get_plan_rule(qs_handle h, int* rule) {
+    if (int rc = check_handle(h)) return rc;
+    if (!rule) return set_error(QS_EINVAL, "qs_get_plan_rule: rule is NULL");
+    rule[0] = h->rule.runs_a;
+    rule[1] = h->rule.split;
+    rule[2] = h->rule.cmin;
+    rule[3] = h->ctas_per_sm;
+    rule[4] = h->pair_cluster;
+    return QS_OK;
+}
+
+// Device time of an evolve of p_trial layers under the handle's plan: the
+// faster of two runs after one warm-up.
+static int time_evolve(qs_handle h, int p_trial, const double* g, const double* b, cudaEvent_t e0, cudaEvent_t e1,
+                       double* ms_out) {
+    double best = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, h->st);
+        if (int rc = qs_evolve(h, p_trial, g, b, 1)) return rc;
+        cudaEventRecord(e1, h->st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) return cuda_error(ce, "qs_autotune");
+        if (int rc = check_device_error(h)) return rc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, (double)ms);  // rep 0 is the warm-up
+    }
+    *ms_out = best;
+    return QS_OK;
+}
+
+int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand_rules, double* cand_ms,
+                   int* best_rule, double* best_ms) {
     if (int rc = check_handle(h)) return rc;
     if (!h->inst.valid) return set_error(QS_ESTATE, "qs_autotune: call qs_set_ising first");
     if (p_trial < 1 || p_trial > 64) return set_error(QS_EINVAL, "qs_autotune: p_trial outside [1, 64]");
-    // candidates: contiguous shape A with the page-bit split, and (complex64,
-    // 24 qubits and more) the run-structured A with three split bits
-    std::vector<ShapeRule> cand{ShapeRule{0, page_bit_for(h->dtype)}};
-    if (h->dtype == QS_C64 && h->nphys >= 24)
-        for (int sp : {20, 22, 24}) cand.push_back(ShapeRule{1, sp});
+    if (max_cand > 0 && (!cand_rules || !cand_ms)) return set_error(QS_EINVAL, "qs_autotune: NULL candidate arrays");
+    struct Cand { ShapeRule r; int cps, cl; double ms; };
+    std::vector<Cand> done;
     std::vector<double> g(p_trial, 0.3), b(p_trial, 0.7);
     const ShapeRule keep = h->rule;
-    double best = 1e300;
-    ShapeRule pick = cand[0];
+    const int keep_cps = h->ctas_per_sm, keep_cl = h->pair_cluster;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     if (ce != cudaSuccess) return cuda_error(ce, "qs_autotune: events");
     int rc = QS_OK;
-    for (const ShapeRule& r : cand) {
+    auto measure = [&](const ShapeRule& r, int cps, int cl) -> double {
+        const bool reshape = r.runs_a != h->rule.runs_a || r.split != h->rule.split || r.cmin != h->rule.cmin;
         h->rule = r;
-        if ((rc = replan(h))) break;
-        if ((rc = qs_evolve(h, p_trial, g.data(), b.data(), 1))) break;  // warm-up
-        cudaEventRecord(e0, h->st);
-        if ((rc = qs_evolve(h, p_trial, g.data(), b.data(), 1))) break;
-        cudaEventRecord(e1, h->st);
-        ce = cudaEventSynchronize(e1);
-        if (ce != cudaSuccess) { rc = cuda_error(ce, "qs_autotune"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; pick = r; }
+        h->ctas_per_sm = cps;
+        h->pair_cluster = cl;
+        double ms = 1e300;
+        if (reshape && (rc = replan(h))) return ms;
+        if ((rc = time_evolve(h, p_trial, g.data(), b.data(), e0, e1, &ms))) return 1e300;
+        done.push_back(Cand{r, cps, cl, ms});
+        return ms;
+    };
+    // stage 1, tile shapes: contiguous shape A with the page-bit split and,
+    // for complex64 states of 24 qubits and more, the run-structured A with
+    // three split bits; strided rows of 2^2 or 2^3 amplitudes
+    std::vector<ShapeRule> shapes{ShapeRule{0, page_bit_for(h->dtype), -1}};
+    if (h->dtype == QS_C64 && h->nphys >= 24)
+        for (int sp : {20, 22, 24}) shapes.push_back(ShapeRule{1, sp, -1});
+    const size_t ns = shapes.size();
+    for (size_t i = 0; i < ns; ++i) shapes.push_back(ShapeRule{shapes[i].runs_a, shapes[i].split, 3});
+    double best = 1e300;
+    Cand pick{shapes[0], 0, 4, 1e300};
+    for (const ShapeRule& r : shapes) {
+        const double ms = measure(r, 0, 4);
+        if (rc) break;
+        if (ms < best) { best = ms; pick = Cand{r, 0, 4, ms}; }
+    }
+    // stage 2, launch: one CTA per SM fewer than fit, and (complex64) the
+    // strided packed-pair sweeps without their 4-CTA clusters
+    if (!rc) {
+        int full = 0;
+        for (int k = 0; k < 3; ++k) full = std::max(full, grid_for(h, k, 0));
+        if (!h->sms) cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+        const int per_sm = h->sms > 0 ? full / h->sms : 0;
+        std::vector<std::pair<int, int>> launch;
+        if (per_sm > 1) launch.push_back({per_sm - 1, 4});
+        if (h->dtype == QS_C64) launch.push_back({0, 1});
+        for (auto [cps, cl] : launch) {
+            const double ms = measure(pick.r, cps, cl);
+            if (rc) break;
+            if (ms < best) { best = ms; pick = Cand{pick.r, cps, cl, ms}; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->rule = rc ? keep : pick;
+    if (rc) {
+        h->rule = keep;
+        h->ctas_per_sm = keep_cps;
+        h->pair_cluster = keep_cl;
+    } else {
+        h->rule = pick.r;
+        h->ctas_per_sm = pick.cps;
+        h->pair_cluster = pick.cl;
+    }
     if (int rc2 = replan(h)) return rc ? rc : rc2;
     if (rc) return rc;
-    if (runs_a) *runs_a = pick.runs_a;
-    if (split) *split = pick.split;
+    if (ncand) *ncand = (int)done.size();
+    for (int i = 0; i < (int)done.size() && i < max_cand; ++i) {
+        const Cand& c = done[i];
+        const int v[5] = {c.r.runs_a, c.r.split, c.r.cmin, c.cps, c.cl};
+        for (int k = 0; k < 5; ++k) cand_rules[5 * i + k] = v[k];
+        cand_ms[i] = c.ms;
+    }
+    if (best_rule) {
+        const int v[5] = {pick.r.runs_a, pick.r.split, pick.r.cmin, pick.cps, pick.cl};
+        for (int k = 0; k < 5; ++k) best_rule[k] = v[k];
+    }
     if (best_ms) *best_ms = best;
+    return QS_OK;
+}
+
+int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_ms) {
+    int rule[5];
+    if (int rc = qs_autotune_ex(h, p_trial, 0, nullptr, nullptr, nullptr, rule, best_ms)) return rc;
+    if (runs_a) *runs_a = rule[0];
+    if (split) *split = rule[1];
     return QS_OK;
 }
 
@@ -409,6 +512,17 @@ int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_
 // Grid size of the persistent sweep kernel for a tile shape.
 static int grid_for(qs_handle h, int kind, int adjoint) {
     int& g = h->grid[adjoint][kind];
+    if (h->ctas_per_sm > 0) {  // the launch rule caps the persistent grid
+        if (!h->sms) cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+        int full = g;
+        if (!full) {
+            const int keep = h->ctas_per_sm;
+            h->ctas_per_sm = 0;
+            full = grid_for(h, kind, adjoint);
+            h->ctas_per_sm = keep;
+        }
+        return std::min(full, h->ctas_per_sm * h->sms);
+    }
     if (!g)
         g = kind < 3    ? sweep_grid(h->dtype, adjoint, kind)
             : adjoint   ? sweep_pair_adj_grid()
@@ -603,6 +717,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
                       reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
         L.pq = &I.pair_q[fwd[i].shape];
+        L.cluster = h->pair_cluster;
         e = launch_sweep(L, forward_grid(h, L), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
         if (zred_cnt[i]) {

@@ -75,6 +75,8 @@ struct qs_batch {
     int grid[2] = {};  // [adjoint]: persistent queue grid
     uint64_t wait_ns = kQueueWaitNs;  // dependency wait limit
     int withhold = -1;  // failure-detection test: the instance whose dependency is withheld
+    int ctas_per_sm = 0;       // launch rule: persistent queue CTAs per SM (0 = as many as fit)
+    int64_t window_bytes = 0;  // queue order: instance windows of at most this many state bytes (0 = one)
     cudaGraphExec_t graph = nullptr;
     bool have_results = false;
     bool poisoned = false;  // a kernel exited with a tile copy possibly still in flight
@@ -84,6 +86,11 @@ struct qs_batch {
 static int bgrid(qs_batch_handle b, int adjoint) {
     int& g = b->grid[adjoint];
     if (!g) g = queue_grid(adjoint);
+    if (b->ctas_per_sm > 0) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        return std::min(g, b->ctas_per_sm * sms);
+    }
     return g;
 }
 
@@ -230,15 +237,37 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
     double* dpart = reinterpret_cast<double*>(b->partials.ptr);
     if (int rc = b->qctl.reserve(64 + (size_t)C * sizeof(unsigned))) return rc;
 
-    // the task list of one queue, wave by wave; task (i, w) needs every tile
-    // of instance i's sweeps 0..w-1
-    auto build_queue = [&](const std::vector<std::vector<PlanSweep>>& L, size_t nw, int adj, QueuePlan& out) {
+    // Instance windows: consecutive instances whose states together hold at
+    // most window_bytes (at least one each; all instances when 0).  Within a
+    // window the queue runs wave by wave, so a window's states can stay in
+    // L2 between its sweeps.
+    std::vector<std::vector<int>> windows;
+    {
+        int64_t acc = 0;
+        for (int i = 0; i < C; ++i) {
+            const int64_t bytes = (int64_t)8 << b->nphys[i];
+            if (windows.empty() || (b->window_bytes > 0 && acc + bytes > b->window_bytes)) {
+                windows.emplace_back();
+                acc = 0;
+            }
+            windows.back().push_back(i);
+            acc += bytes;
+        }
+    }
+    (void)maxf;
+    (void)maxr;
+    // the task list of one queue, window by window and wave by wave inside a
+    // window; task (i, w) needs every tile of instance i's sweeps 0..w-1
+    auto build_queue = [&](const std::vector<std::vector<PlanSweep>>& L, int adj, QueuePlan& out) {
         std::vector<SweepTask> tasks;
         std::vector<int64_t> pre{0}, need(C, 0);
         std::vector<ReduceTask> rts;
         int64_t pbase = 0;
-        for (size_t w = 0; w < nw; ++w) {
-            for (int i = 0; i < C; ++i) {
+        for (const std::vector<int>& win : windows) {
+          size_t nw = 0;
+          for (int i : win) nw = std::max(nw, L[i].size());
+          for (size_t w = 0; w < nw; ++w) {
+            for (int i : win) {
                 if (w >= L[i].size()) continue;
                 const PlanSweep& s = L[i][w];
                 const Instance& I = b->inst[i];
@@ -299,6 +328,7 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
                 tasks.push_back(t);
                 pre.push_back(pre.back() + sh.ntiles);
             }
+          }
         }
         out.ntasks = (int)tasks.size();
         out.total = pre.back();
@@ -336,8 +366,8 @@ static int build_plan(qs_batch_handle b, bool grad, int objective) {
     if (queue_tiles(fwd, 0) > kQueueMaxTiles || (grad && queue_tiles(rev, 1) > kQueueMaxTiles))
         return set_error(QS_EINVAL, "batch too large: more than %lld tiles in one work queue; split the batch",
                          (long long)kQueueMaxTiles);
-    build_queue(fwd, maxf, 0, b->fwd_q);
-    if (grad) build_queue(rev, maxr, 1, b->rev_q);
+    build_queue(fwd, 0, b->fwd_q);
+    if (grad) build_queue(rev, 1, b->rev_q);
     else b->rev_q = QueuePlan{};
 
     // preparation tasks (angles live in b->angles: [gamma_all, beta_all])
@@ -463,6 +493,76 @@ int qs_batch_evolve(qs_batch_handle b, const int* p, const int64_t* angle_off, c
     }
     if (rc) return rc;
     b->have_results = true;
+    return QS_OK;
+}
+
+int qs_batch_set_launch_rule(qs_batch_handle b, int ctas_per_sm, int64_t window_bytes) {
+    if (int rc = check_batch(b)) return rc;
+    if (ctas_per_sm < 0 || ctas_per_sm > 32 || window_bytes < 0)
+        return set_error(QS_EINVAL, "qs_batch_set_launch_rule: ctas_per_sm in [0, 32], window_bytes >= 0");
+    b->ctas_per_sm = ctas_per_sm;
+    if (window_bytes != b->window_bytes) b->planned = false;
+    b->window_bytes = window_bytes;
+    drop_graph(b);
+    return QS_OK;
+}
+
+int qs_batch_autotune(qs_batch_handle b, int* ctas_per_sm, int64_t* window_bytes, double* best_ms) {
+    if (int rc = check_batch(b)) return rc;
+    if ((int)b->p.size() != b->count) return set_error(QS_ESTATE, "qs_batch_autotune: call qs_batch_evolve first");
+    cudaSetDevice(b->device);
+    const int keep_c = b->ctas_per_sm;
+    const int64_t keep_w = b->window_bytes;
+    const int per_sm = std::max(1, bgrid(b, 0) / std::max(1, [&] {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        return sms;
+    }()));
+    std::vector<int> ctas{0};
+    if (per_sm > 1) ctas.push_back(per_sm - 1);
+    const int64_t windows[3] = {0, (int64_t)256 << 20, (int64_t)64 << 20};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) return cuda_error(ce, "qs_batch_autotune: events");
+    int rc = QS_OK;
+    double best = 1e300;
+    int pick_c = 0;
+    int64_t pick_w = 0;
+    for (int64_t w : windows) {
+        for (int c : ctas) {
+            b->ctas_per_sm = c;
+            if (w != b->window_bytes) b->planned = false;
+            b->window_bytes = w;
+            if (!b->planned || b->plan_grad)
+                if ((rc = build_plan(b, false, 0))) break;
+            double ms = 1e300;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {  // one warm-up, the faster of two runs
+                cudaEventRecord(e0, b->st);
+                rc = run_step(b, false);
+                cudaEventRecord(e1, b->st);
+                if (!rc && (ce = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_error(ce, "qs_batch_autotune");
+                if (!rc) rc = batch_check_err(b);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, (double)t);
+            }
+            if (rc) break;
+            if (ms < best) { best = ms; pick_c = c; pick_w = w; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->ctas_per_sm = rc ? keep_c : pick_c;
+    b->window_bytes = rc ? keep_w : pick_w;
+    b->planned = false;
+    drop_graph(b);
+    if (rc) return rc;
+    b->have_results = false;
+    if (ctas_per_sm) *ctas_per_sm = pick_c;
+    if (window_bytes) *window_bytes = pick_w;
+    if (best_ms) *best_ms = best;
     return QS_OK;
 }
 

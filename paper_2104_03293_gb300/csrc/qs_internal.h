@@ -136,6 +136,7 @@ struct SweepLaunch {
     int pairc = 0;                 // 2 or 3: packed-pair kernel for carried bits c (qs_pair.h)
     const PairQ* pq = nullptr;     // host: Q tables of the shape (packed-pair forward sweeps)
     const PairAdjQ* paq = nullptr; // host: Q tables of the shape (packed-pair adjoint sweeps)
+    int cluster = 4;               // strided packed-pair forward: 4-CTA clusters (line sharing) or 1
 };
 
 // Cost program: the Ising cost of Eq. (HC) specialised to one register layout.

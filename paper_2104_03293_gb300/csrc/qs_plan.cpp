@@ -171,7 +171,7 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, Sh
         if (a.g0 + a.n1 != nphys || a.g1 != kRunBits || a.c + a.n1 + 1 != cfg.K_A) return {};
     }
     v.push_back(a);
-    const int per = cfg.K_B - cfg.c_min;                   // targets per strided shape
+    const int per = cfg.K_B - (rule.cmin >= 0 ? rule.cmin : cfg.c_min);  // targets per strided shape
     const int rest = hi - lo;
     if (rest <= 0) return v;
     const int S = (rest + per - 1) / per;                  // strided shapes

@@ -61,10 +61,12 @@ inline int page_bit_for(int dtype) { return dtype == 0 ? 18 : 17; }
 // shape A run-structured (complex64, K = 13), 0 contiguous, -1 the default
 // rule (run-structured from 33 qubits); split = index bit from which the
 // strided shapes' qubits are dealt out evenly, -1 = default (bit 22 with a
-// run-structured A, else the 2 MB page bit).
+// run-structured A, else the 2 MB page bit); cmin = carried bits of the
+// strided shapes (each holds 13 - cmin targets in rows of 2^cmin amplitudes).
 struct ShapeRule {
     int runs_a = -1;
     int split = -1;
+    int cmin = -1;  // carried low bits of the strided shapes (2 or 3; -1 = the kernel default, 2)
 };
 std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, ShapeRule rule = ShapeRule{});
 void shape_regq(const Shape& s, int R, int g, int* regq);

@@ -57,6 +57,11 @@ _SIGS = {
     "qs_enumerate_noalloc": [_I, _PD, _I, _PI32, _PD, _P, _PI64, _PI64, _PI64, _PI64, _PI],
     "qs_set_shape_rule": [_P, _I, _I],
     "qs_autotune": [_P, _I, _PI, _PI, _PD],
+    "qs_set_plan_rule": [_P, _PI],
+    "qs_get_plan_rule": [_P, _PI],
+    "qs_autotune_ex": [_P, _I, _I, _PI, _PI, _PD, _PI, _PD],
+    "qs_batch_set_launch_rule": [_P, _I, ctypes.c_int64],
+    "qs_batch_autotune": [_P, _PI, _PI64, _PD],
     "qs_grad": [_P, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "qs_evolve_zexp": [_P, _I, _PD, _PD, _PD],
     "qs_set_adjoint_buffer": [_P, _P, ctypes.c_size_t],
@@ -83,6 +88,19 @@ _SIGS = {
     "qs_batch_test_withhold": [_P, _I, _D],
     "qs_batch_partition": [_I, _PI, _PI, _I, _PI, _PD],
 }
+
+
+def _tune_key(n: int, dtype: int) -> str:
+    """Autotuner cache key: GPU model, SM count, n and dtype."""
+    name, sms = "gpu", 0
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pr = torch.cuda.get_device_properties(torch.cuda.current_device())
+            name, sms = pr.name, pr.multi_processor_count
+    except Exception:
+        pass
+    return f"{name}|sm{sms}|n{n}|{'c64' if dtype == QS_C64 else 'c128'}"
 
 
 def header_functions() -> list[str]:
@@ -249,6 +267,50 @@ class State:
         r, sp, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(lib().qs_autotune(self._h, int(p_trial), ctypes.byref(r), ctypes.byref(sp), ctypes.byref(ms)))
         return r.value, sp.value, ms.value
+
+    def plan_rule(self) -> tuple:
+        """(runs_a, split, cmin, ctas_per_sm, pair_cluster) of the handle."""
+        v = (ctypes.c_int * 5)()
+        _check(lib().qs_get_plan_rule(self._h, v))
+        return tuple(v)
+
+    def set_plan_rule(self, rule):
+        v = (ctypes.c_int * 5)(*[int(x) for x in rule])
+        _check(lib().qs_set_plan_rule(self._h, v))
+
+    def autotune_plan(self, p_trial: int = 2, cache: Optional[str] = None):
+        """Search the plan rules (qs_autotune_ex) and keep the fastest.  Returns
+        (rule, ms, candidates) with candidates a list of (rule, ms).  With a
+        JSON cache file (argument or QS_TUNE_CACHE), a rule stored for this
+        GPU model, SM count, n and dtype is applied without timing, and a new
+        search is stored there."""
+        cache = cache or os.environ.get("QS_TUNE_CACHE")
+        key = _tune_key(self.n, self.dtype)
+        if cache and os.path.exists(cache):
+            import json
+            with open(cache) as f:
+                entry = json.load(f).get(key)
+            if entry:
+                self.set_plan_rule(entry["rule"])
+                return tuple(entry["rule"]), float(entry["ms"]), [(tuple(r), m) for r, m in entry["candidates"]]
+        cap = 64
+        rules, ms_c = (ctypes.c_int * (5 * cap))(), (ctypes.c_double * cap)()
+        best, nc, ms = (ctypes.c_int * 5)(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().qs_autotune_ex(self._h, int(p_trial), cap, ctypes.byref(nc), rules, ms_c, best, ctypes.byref(ms)))
+        cands = [(tuple(rules[5 * i:5 * i + 5]), ms_c[i]) for i in range(min(nc.value, cap))]
+        if cache:
+            import json
+            data = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    data = json.load(f)
+            data[key] = {"rule": list(best), "ms": ms.value, "p_trial": int(p_trial),
+                         "candidates": [[list(r), m] for r, m in cands]}
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1)
+            os.replace(tmp, cache)
+        return tuple(best), ms.value, cands
 
     def set_adjoint_buffer(self, buffer):
         self._adj = buffer
@@ -421,6 +483,17 @@ class Batch:
         dg, db = np.zeros(max(tot, 1)), np.zeros(max(tot, 1))
         _check(lib().qs_batch_grad(self._h, int(objective), _dptr(v), _dptr(dg), _dptr(db)))
         return v, self._split(dg), self._split(db)
+
+    def set_launch_rule(self, ctas_per_sm: int = 0, window_bytes: int = 0):
+        _check(lib().qs_batch_set_launch_rule(self._h, int(ctas_per_sm), int(window_bytes)))
+
+    def autotune(self):
+        """Time the queue's launch rules on the last evolve's angles, keep the
+        fastest: (ctas_per_sm, window_bytes, ms).  A new evolve is needed
+        before results()."""
+        c, w, ms = ctypes.c_int(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().qs_batch_autotune(self._h, ctypes.byref(c), ctypes.byref(w), ctypes.byref(ms)))
+        return c.value, w.value, ms.value
 
     def test_withhold(self, idx: int, wait_limit_s: float):
         """Failure-detection test: the next evolve withholds one dependency of

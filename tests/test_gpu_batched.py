@@ -216,3 +216,34 @@ def test_queue_withheld_dependency_times_out(qs):
     for i, inst in enumerate(insts):
         Er, Pr, _ = oracle.readout(inst, oracle.evolve(inst, gs[i], bs[i]))
         assert_readout(inst, E[i], P[i], Er, Pr, i)
+
+
+def test_batch_launch_rules_and_autotune(qs):
+    """Every work-queue launch rule (CTAs per SM, instance windows that
+    order the queue window by window) gives the oracle's readouts and
+    gradients; the batch autotuner keeps one of them."""
+    items = I.config2(count=10, n_lo=13, n_hi=19, p_lo=1, p_hi=5)
+    insts = [inst for inst, _, _ in items]
+    gs, bs = [g for _, g, _ in items], [b for _, _, b in items]
+    bt = _batch(qs, insts)
+    ref = [oracle.readout(x, oracle.evolve(x, g, b))[:2] for x, g, b in items]
+    adj = [oracle.adjoint(x, g, b, 0) for x, g, b in items]
+    try:
+        for rule in [(0, 0), (1, 0), (0, 1 << 20), (1, 4 << 20), (0, 1)]:
+            bt.set_launch_rule(*rule)
+            bt.evolve(gs, bs)
+            E, P = bt.results()
+            for i, inst in enumerate(insts):
+                assert_readout(inst, E[i], P[i], ref[i][0], ref[i][1], (rule, i))
+            v, dg, db = bt.grad(0)
+            for i, inst in enumerate(insts):
+                assert_grad(np.concatenate([dg[i], db[i]]), np.concatenate([adj[i][1], adj[i][2]]), what=(rule, i))
+        bt.evolve(gs, bs)
+        c, w, ms = bt.autotune()
+        assert c in (0, 1) and w in (0, 256 << 20, 64 << 20) and ms > 0
+        bt.evolve(gs, bs)
+        E, P = bt.results()
+        for i, inst in enumerate(insts):
+            assert_readout(inst, E[i], P[i], ref[i][0], ref[i][1], ("tuned", i))
+    finally:
+        bt.close()

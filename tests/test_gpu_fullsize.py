@@ -197,6 +197,41 @@ def test_shape_rules_and_autotuner(qs):
     st.close()
 
 
+def test_plan_rule_search_every_candidate_and_cache(qs, tmp_path):
+    """The full plan-rule search at n = 24 (shape A form and split bit,
+    strided rows of 2^2 or 2^3 amplitudes, CTAs per SM, clustered or plain
+    strided sweeps): every measured candidate gives the oracle's state,
+    readout and gradient; the kept rule is the fastest measured one; a JSON
+    cache applies the stored rule to a new handle without timing."""
+    inst = I.erdos_renyi_ising(24, I.workload_seed(5, 201), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    g, b = _angles(6)
+    ref = oracle.evolve(inst, g, b)
+    Er, Pr, _ = oracle.readout(inst, ref)
+    vr, dgr, dbr = oracle.adjoint(inst, g, b, 0)
+    cache = str(tmp_path / "tune.json")
+    st = qs.State(inst.n)
+    st.set_instance(inst)
+    best, ms, cands = st.autotune_plan(2, cache=cache)
+    assert len(cands) >= 8 and ms == min(m for _, m in cands)
+    assert best in [r for r, _ in cands] and st.plan_rule() == best
+    assert {r[2] for r, _ in cands} == {-1, 3} and {r[4] for r, _ in cands} == {1, 4}
+    for rule, _ in cands:
+        st.set_plan_rule(rule)
+        st.evolve(g, b)
+        E, P, _ = st.readout()
+        assert np.linalg.norm(st.copy_state() - ref) <= 1e-4, rule
+        assert abs(E - Er) <= e_tol(inst, Er) and abs(P - Pr) <= p_tol(Pr), rule
+        v, dg, db = st.grad(g, b, 0)
+        assert abs(v - vr) <= e_tol(inst, vr), rule
+        assert_grad(np.concatenate([dg, db]), np.concatenate([dgr, dbr]), what=rule)
+    st.close()
+    st2 = qs.State(inst.n)
+    st2.set_instance(inst)
+    best2, ms2, cands2 = st2.autotune_plan(2, cache=cache)
+    assert best2 == best and ms2 == ms and st2.plan_rule() == best and len(cands2) == len(cands)
+    st2.close()
+
+
 @pytest.mark.slow
 def test_connected_n34_p20_against_plain_path_and_host_enumeration(qs):
     """The benchmark's own connected n = 34 instance (ER(4), h, J in U{-1,0,1},
