@@ -18,6 +18,8 @@ formulas that are plain algebra:
 * the paper's second-order map, Eqs. (beta_k)-(gamma_k) verbatim;
 * the chain rule from (dgamma, dbeta) to (dtau, ds_k) for both maps;
 * the per-layer spin expectations <Z_i> recorded during AQA (in ``oracle.c``);
+* quantum spin dynamics by the product formula of Eq. (AQA4), step by step,
+  with exact single-spin x + z exponentials (in ``oracle.c``);
 * a float64 Adam step (bias-corrected) used to drive oracle gradients;
 * the exact-cover objective of Eq. (exactcover) from its definition, over
   all assignments (the pin of the exact-cover to Ising mapping).
@@ -81,6 +83,8 @@ def _load():
         lib.orc_adjoint.argtypes = [I, P, I, P, P, I, P, P, I, D, P, P, P, P, P]
         lib.orc_zexp.argtypes = [I, P, P]
         lib.orc_evolve_zexp.argtypes = [I, P, P, I, P, P, I, P, P, P]
+        lib.orc_gate_u.argtypes = [I, P, I, P]
+        lib.orc_qsds_evolve.argtypes = [I, P, P, I, P, P, I, D, P, P]
         lib.orc_set_threads.argtypes = [I]
         lib.orc_num_threads.restype = I
         _lib = lib
@@ -188,6 +192,28 @@ def readout(inst, psi, cmin=None):
     _load().orc_readout(inst.n, _ptr(psi), _ptr(h), e.shape[0], _ptr(e), _ptr(J), float(cmin),
                         _ptr(E), _ptr(P), _ptr(nrm))
     return float(E[0]), float(P[0]), float(nrm[0])
+
+
+def gate_u(n, psi, j, u) -> np.ndarray:
+    """Apply the 2 x 2 matrix u (complex, [[u00, u01], [u10, u11]]) to qubit j
+    of psi in place (Eq. twocomponentupdates with a general matrix)."""
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(4).view(np.float64))
+    _load().orc_gate_u(n, _ptr(psi), int(j), _ptr(uu))
+    return psi
+
+
+def qsds_evolve(inst, tau, A, B) -> np.ndarray:
+    """The second-order product formula of Eq. (AQA4), step by step from
+    |+>^n, with the fields of Eq. (AQA3): per step S(tau/2) Z(tau) S(tau/2),
+    S = exp[i tau/2 sum_i (A_l X_i - B_l h_i Z_i)], Z = exp[-i tau B_l sum J Z Z]."""
+    h, e, J = _fields(inst)
+    a = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(B, dtype=np.float64)
+    assert a.shape == b.shape
+    psi = np.empty(1 << inst.n, dtype=np.complex128)
+    _load().orc_qsds_evolve(inst.n, _ptr(psi), _ptr(h), e.shape[0], _ptr(e), _ptr(J), a.size, float(tau),
+                            _ptr(a), _ptr(b))
+    return psi
 
 
 def zexp(inst, psi) -> np.ndarray:

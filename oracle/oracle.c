@@ -279,6 +279,62 @@ void orc_evolve_zexp(int n, cplx* psi, const double* h, int m, const int32_t* ed
     }
 }
 
+/* Eq. (twocomponentupdates) with a general 2 x 2 matrix u (row major,
+ * u = [u00, u01, u10, u11] as re, im pairs): for every pair (z, z + 2^j)
+ * with bit j of z clear, (a, b) -> (u00 a + u01 b, u10 a + u11 b). */
+void orc_gate_u(int n, cplx* psi, int j, const double* u)
+{
+    uint64_t N = (uint64_t)1 << n, step = (uint64_t)1 << j;
+    const cplx u00 = u[0] + I * u[1], u01 = u[2] + I * u[3], u10 = u[4] + I * u[5], u11 = u[6] + I * u[7];
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < (int64_t)N; ++z) {
+        if ((uint64_t)z & step) continue;
+        cplx a = psi[z], b = psi[(uint64_t)z + step];
+        psi[z] = u00 * a + u01 * b;
+        psi[(uint64_t)z + step] = u10 * a + u11 * b;
+    }
+}
+
+/* exp(i theta (a X + b Z)) of one spin: cos(theta r) + i sin(theta r) (a X + b Z) / r,
+ * r = sqrt(a^2 + b^2) (the identity when r = 0). */
+static void spin_exp(double theta, double a, double b, double* u)
+{
+    double r = sqrt(a * a + b * b);
+    double c = cos(theta * r), sr = r > 0.0 ? sin(theta * r) / r : 0.0;
+    cplx u00 = c + I * sr * b, u01 = I * sr * a, u11 = c - I * sr * b;
+    u[0] = creal(u00); u[1] = cimag(u00);
+    u[2] = creal(u01); u[3] = cimag(u01);
+    u[4] = creal(u01); u[5] = cimag(u01);
+    u[6] = creal(u11); u[7] = cimag(u11);
+}
+
+/*
+ * Quantum spin dynamics by the second-order product formula of Eq. (AQA4),
+ * step by step as written: for l = 0..nsteps-1,
+ *   S_l(tau/2) = exp[i tau/2 sum_i (A_l sigma^x_i - B_l h_i sigma^z_i)],
+ *   Z_l(tau)   = exp[-i tau B_l sum_{ij} J_ij sigma^z_i sigma^z_j],
+ *   psi <- S_l(tau/2) Z_l(tau) S_l(tau/2) psi,
+ * from |+>^n, with the fields of Eq. (AQA3) (h~^x = A, h~^z_i = -B h_i,
+ * J~^z_ij = -B J_ij).  Each single-spin exponential is the exact 2 x 2
+ * matrix; each coupling an exp(-i theta Z_i Z_j) gate.
+ */
+void orc_qsds_evolve(int n, cplx* psi, const double* h, int m, const int32_t* edges, const double* J,
+                     int nsteps, double tau, const double* A, const double* B)
+{
+    double u[8];
+    orc_init_plus(n, psi);
+    for (int l = 0; l < nsteps; ++l) {
+        for (int half = 0; half < 2; ++half) {
+            for (int i = 0; i < n; ++i) {
+                spin_exp(0.5 * tau, A[l], -B[l] * h[i], u);
+                orc_gate_u(n, psi, i, u);
+            }
+            if (half == 0)
+                for (int e = 0; e < m; ++e) orc_gate_zz(n, psi, edges[2 * e], edges[2 * e + 1], tau * B[l] * J[e]);
+        }
+    }
+}
+
 /* Host threads used by the OpenMP loops above (timing of the CPU baseline
  * with all cores and with one). */
 void orc_set_threads(int t)

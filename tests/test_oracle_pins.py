@@ -360,3 +360,61 @@ def test_adam_matches_torch():
         t_param.grad = torch.tensor(grad, dtype=torch.float64)
         opt.step()
         assert np.max(np.abs(theta - t_param.detach().numpy())) <= 1e-14
+
+
+# ------------------------------------------------ QSDS product formula, Eq. (AQA4)
+def _dense_qsds(inst, tau, A, B):
+    n = inst.n
+    psi = np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)
+    HX = dense_hd(n)
+    HZ = sum(inst.h[i] * pauli(n, {i: PZ}) for i in range(n))
+    HZZ = dense_hc(inst) - HZ
+    for a, b in zip(A, B):
+        S = scipy.linalg.expm(0.5j * tau * (a * HX - b * HZ))  # h~x = A, h~z = -B h
+        Zc = scipy.linalg.expm(-1j * tau * b * HZZ)            # J~z = -B J
+        psi = S @ (Zc @ (S @ psi))
+    return psi
+
+
+@pytest.mark.parametrize("idx", range(4))
+def test_qsds_matches_dense_product_formula(idx):
+    """Eq. (AQA4) with the fields of Eq. (AQA3): the oracle's single-spin
+    2 x 2 exponentials and ZZ gates against dense matrix exponentials of the
+    full single-spin and coupling Hamiltonians, step by step."""
+    inst = small_instances()[idx]
+    nsteps = 5
+    s = np.arange(nsteps) / nsteps
+    A, B = 1.0 - s, s
+    got = oracle.qsds_evolve(inst, 0.6, A, B)
+    want = _dense_qsds(inst, 0.6, A, B)
+    assert np.max(np.abs(got - want)) <= 1e-12
+    assert abs(np.linalg.norm(got) - 1.0) <= 1e-13
+
+
+def test_qsds_without_fields_is_the_second_order_qaoa_map():
+    """With h = 0 the single-spin steps are pure x rotations that commute, so
+    merging consecutive half steps gives the QAOA state with gamma_k =
+    tau B_k and beta_k = -tau (A_k + A_{k+1}) / 2 (the last one -tau A / 2),
+    up to the global phase exp(i tau A_0 n / 2) of the first half step on
+    |+>^n (the structure of Appendix A)."""
+    inst = I.maxcut_regular3(8, 91)
+    nsteps, tau = 6, 0.45
+    s = (np.arange(nsteps) + 0.5) / nsteps
+    A, B = 1.0 - s, s
+    got = oracle.qsds_evolve(inst, tau, A, B)
+    g = tau * B
+    b = -0.5 * tau * (A + np.append(A[1:], 0.0))
+    want = oracle.evolve(inst, g, b) * np.exp(0.5j * tau * A[0] * inst.n)
+    assert np.max(np.abs(got - want)) <= 1e-12
+
+
+def test_gate_u_general_matrix():
+    """A general 2 x 2 matrix on qubit j against the dense Kronecker product."""
+    rng = np.random.default_rng(5)
+    n = 5
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    u = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    for j in range(n):
+        want = pauli(n, {j: u}) @ psi
+        got = oracle.gate_u(n, psi.copy(), j, u)
+        assert np.max(np.abs(got - want)) <= 1e-12
