@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
                 to_layout(0);
                 S::template rotate<0>(X, Y, w);
             }
-            if (kPhase && rd.phase_post) do_phase(ltab, ly.frame, rd.layer == slayer);
+            // (forward plans apply a layer's phase before its rotations only:
+            // no phase_post here, which keeps the register pressure down)
         }
         to_layout(0);
 
@@ -435,7 +436,7 @@ static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (L.total_tiles % 4 == 0 && grid % 4 == 0 && grid >= 4) {
+    if (L.cluster == 4 && L.total_tiles % 4 == 0 && grid % 4 == 0 && grid >= 4) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(PairSweep<C>::NT);

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(128, 3)
                 to_layout(0);
                 S::rotate<0>(X, Y, w);
             }
-            if (kPhase && rd.phase_post) do_phase(ltab, ly.frame, rd.layer == slayer);
+            // (forward plans apply a layer's phase before its rotations only)
         }
         to_layout(0);
 
