@@ -276,6 +276,20 @@ def secondary_workloads(qs, I, torch):
         out[f"autotune_n{nt}"] = {"kept": list(kept), "kept_ms_p8": full[tuple(kept)], "best_ms_p8": best,
                                   "kept_over_best": full[tuple(kept)] / best,
                                   "candidates_ms_p8": [[list(r), m] for r, m in full.items()]}
+    # product formula of Eq. (AQA4) (single-spin x + z unitaries) at n = 30,
+    # 20 steps, against the transverse-field evolve of the same layer count
+    x = I.erdos_renyi_ising(30, I.workload_seed(5, 330), h_values=(-1, 0, 1), j_values=(-1, 0, 1))
+    sq = (np.arange(20) + 0.5) / 20
+    gq, uq = qs.qsds_layers(30, 0.75, 1.0 - sq, sq, x.h)
+    st = qs.State(30)
+    st.set_ising(x.h, x.edges, x.J)
+    t_su2 = timed(lambda: st.evolve_su2(gq, uq), 3)
+    _, Pq, _ = st.readout()
+    gg, bb = qs.aqa_angles(0.75, np.arange(1, 22) / 22.0)
+    t_x = timed(lambda: st.evolve(gg, bb), 3)
+    st.close()
+    out["qsds_n30_20steps"] = {"ms": t_su2, "layers": len(gq), "transverse_field_evolve_ms": t_x,
+                               "ratio": t_su2 / t_x, "P_ground": Pq}
     # batched queue: launch rules timed on the 512-instance forward
     bt = qs.Batch([x.n for x in insts512])
     for i, x in enumerate(insts512):

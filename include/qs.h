@@ -134,6 +134,31 @@ int qs_evolve(qs_handle h, int p, const double* gamma, const double* beta, int f
  * QS_ETIMEOUT. */
 int qs_evolve_zexp(qs_handle h, int p, const double* gamma, const double* beta, double* zexp);
 
+/* Layers with general single-spin unitaries in place of the transverse-field
+ * mixer (the combined x + z single-spin exponentials of the product formula
+ * Eq. (AQA4)): from |+>^n, for k = 0..p-1,
+ *   psi <- (prod_i U_{k,i}) exp(-i gamma_k H_C) psi,
+ * with H_C the handle's Ising cost (Eq. HC).
+ *   gamma  p host doubles;
+ *   u      p * n * 8 host doubles: U_{k,i} = [[u00, u01], [u10, u11]] row
+ *          major, each entry (re, im), acting on (|0>, |1>) of qubit i.
+ * The matrices need not be unitary for the arithmetic, but the readout's
+ * meaning assumes they are.  The readout of the final state is cached as
+ * after qs_evolve.  Tiled path only; complex64 and complex128; no adjoint.
+ * Asynchronous.  Errors: QS_EINVAL, QS_ESTATE, QS_ECUDA. */
+int qs_evolve_su2(qs_handle h, int p, const double* gamma, const double* u);
+
+/* The layers of qs_evolve_su2 that reproduce nsteps steps of Eq. (AQA4)
+ * with the fields of Eq. (AQA3) (h~^x = A_l, h~^z_i = -B_l h_i, J~^z_ij =
+ * -B_l J_ij; A, B nsteps doubles, hfield n doubles): consecutive half steps
+ * S_{l+1}(tau/2) S_l(tau/2) are merged into one matrix per qubit, and since
+ * the engine's phase exp(-i gamma H_C) includes the fields, their part
+ * exp(-i tau B_l h_i Z_i) is undone in the following matrices.  Writes
+ * nsteps + 1 layers: gamma (nsteps + 1 doubles) and u ((nsteps + 1) n 8
+ * doubles).  Host only.  Errors: QS_EINVAL. */
+int qs_qsds_layers(int n, int nsteps, double tau, const double* A, const double* B, const double* hfield,
+                   double* gamma, double* u);
+
 /* <H_C> of the current state, accumulated in FP64.  Synchronises. */
 int qs_expect(qs_handle h, double* E);
 

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqs.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qs_sweep_c64f.cu", "qs_sweep_other.cu", "qs_sweep_zexp.cu", "qs_sweep_pair.cu", "qs_sweep_runs.cu", "qs_sweep_pair_adj.cu", "qs_sweep.cu", "qs_misc.cu", "qs_api.cu", "qs_batch.cu", "qs_queue.cu", "qs_plan.cpp"]
+SOURCES = ["qs_sweep_c64f.cu", "qs_sweep_other.cu", "qs_sweep_zexp.cu", "qs_sweep_su2.cu", "qs_sweep_pair.cu", "qs_sweep_runs.cu", "qs_sweep_pair_adj.cu", "qs_sweep.cu", "qs_misc.cu", "qs_api.cu", "qs_batch.cu", "qs_queue.cu", "qs_plan.cpp"]
 
 
 def nvcc() -> str:

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -221,7 +222,7 @@ struct qs_state {
     bool own_lam = false;
     Instance inst;
     DevBuf enum_scratch, layers_f, layers_r, tab_f, tab_r, partials, out, frame, err, zpart, zout;
-    Uploader up, up_ang;
+    Uploader up, up_ang, up_su2;
     double theta_pad = 0.0;   // global phase of the idle padding qubits
     bool have_readout = false;
     int grid[2][7] = {};  // [adjoint][kernel kind; 3, 4, 5 = packed-pair kernel, phase / lean / zexp; 6 = runs]
@@ -619,7 +620,8 @@ struct CallBlob {
 // zexp: every sweep holding a layer boundary (a phase of layer k >= 1) or the
 // readout also records <Z_q> of the state after layer k - 1 (resp. p - 1)
 // into per-CTA records, reduced after the sweep into h->zout[layer][n].
-static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective, bool zexp = false) {
+static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective, bool zexp = false,
+                     const double* su2 = nullptr) {
     Instance& I = h->inst;
     const std::vector<Shape>& shf = I.shapes[0];
     const std::vector<Shape>& sha = I.shapes[1];
@@ -629,6 +631,8 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         fwd.back().flags |= T_WRITE_LAM;
         rev = plan_reverse(fwd, sha, p);
     }
+    if (su2)
+        for (auto& s : fwd) s.flags |= T_SU2;
     if (zexp) {
         for (auto& s : fwd) {
             bool rec = (s.flags & T_READOUT) != 0;
@@ -664,6 +668,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         if (pc)
             for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_pair[s.shape][g < 2 ? g : 0]);
         t.zpart = dzp;
+        t.su2 = su2;
         fwd_off.push_back(blob.add(&t, sizeof t));
         const int64_t pre[2] = {0, shf[s.shape].ntiles};
         fwd_pre.push_back(blob.add(pre, sizeof pre));
@@ -831,6 +836,35 @@ int qs_evolve_zexp(qs_handle h, int p, const double* gamma, const double* beta, 
         if (e != cudaSuccess) return cuda_error(e, "qs_evolve_zexp");
     }
     return check_device_error(h);
+}
+
+int qs_evolve_su2(qs_handle h, int p, const double* gamma, const double* u) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->inst.valid) return set_error(QS_ESTATE, "qs_evolve_su2: call qs_set_ising first");
+    if (h->path != QS_PATH_TILED) return set_error(QS_EINVAL, "qs_evolve_su2: needs the tiled path");
+    if (p < 0 || p > QS_MAX_LAYERS_PREP) return set_error(QS_EINVAL, "qs_evolve_su2: p = %d outside [0, %d]", p, QS_MAX_LAYERS_PREP);
+    if (p > 0 && (!gamma || !u)) return set_error(QS_EINVAL, "qs_evolve_su2: gamma or u is NULL");
+    for (int k = 0; k < p; ++k)
+        if (!std::isfinite(gamma[k])) return set_error(QS_EINVAL, "qs_evolve_su2: non-finite gamma at layer %d", k);
+    for (size_t i = 0; i < (size_t)p * h->n * 8; ++i)
+        if (!std::isfinite(u[i])) return set_error(QS_EINVAL, "qs_evolve_su2: non-finite matrix entry %zu", i);
+    // per layer, the n given matrices and the identity on padded idle qubits
+    std::vector<double> U((size_t)std::max(p, 1) * h->nphys * 8, 0.0);
+    for (int k = 0; k < p; ++k)
+        for (int q = 0; q < h->nphys; ++q) {
+            double* d = U.data() + ((size_t)k * h->nphys + q) * 8;
+            if (q < h->n) std::memcpy(d, u + ((size_t)k * h->n + q) * 8, 8 * sizeof(double));
+            else { d[0] = 1.0; d[6] = 1.0; }
+        }
+    if (int rc = h->up_su2.upload(U.data(), U.size() * sizeof(double), h->st)) return rc;
+    std::vector<double> zero((size_t)std::max(p, 1), 0.0);
+    if (int rc = prepare_layers(h, p, gamma, zero.data(), true, false, true)) return rc;  // pure phase tables
+    if (int rc = run_tiled(h, p, true, 0, 0, false, reinterpret_cast<const double*>(h->up_su2.dev.ptr))) return rc;
+    cudaError_t e = cudaMemsetAsync(h->frame.ptr, 0, sizeof(int), h->st);
+    if (e != cudaSuccess) return cuda_error(e, "qs_evolve_su2 frame");
+    h->theta_pad = 0.0;
+    h->have_readout = true;
+    return QS_OK;
 }
 
 int qs_readout(qs_handle h, double* E, double* P, double* norm) {
@@ -1066,6 +1100,51 @@ int qs_aqa_chain_2nd(int p, double tau, const double* s, const double* dgamma, c
         ds[k] += 0.5 * tau * dbeta[k];
     }
     *dtau = t;
+    return QS_OK;
+}
+
+int qs_qsds_layers(int n, int nsteps, double tau, const double* A, const double* B, const double* hfield,
+                   double* gamma, double* u) {
+    if (n < 1 || n > QS_MAX_QUBITS_C64 || nsteps < 0 || nsteps + 1 > QS_MAX_LAYERS_PREP || !std::isfinite(tau))
+        return set_error(QS_EINVAL, "qs_qsds_layers: bad n, nsteps or tau");
+    if ((nsteps > 0 && (!A || !B || !hfield)) || !gamma || !u) return set_error(QS_EINVAL, "qs_qsds_layers: NULL argument");
+    using cd = std::complex<double>;
+    struct M2 { cd a, b, c, d; };  // [[a, b], [c, d]]
+    auto mul = [](const M2& x, const M2& y) {
+        return M2{x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+    };
+    // exp(i theta (ax X + bz Z)) = cos(theta r) + i sin(theta r) (ax X + bz Z) / r
+    auto spin = [](double theta, double ax, double bz) {
+        const double r = std::sqrt(ax * ax + bz * bz), c = std::cos(theta * r);
+        const double sr = r > 0.0 ? std::sin(theta * r) / r : 0.0;
+        const cd i(0.0, 1.0);
+        return M2{c + i * sr * bz, i * sr * ax, i * sr * ax, c - i * sr * bz};
+    };
+    const M2 id{1.0, 0.0, 0.0, 1.0};
+    auto put = [&](int layer, int q, const M2& m) {
+        double* d = u + ((size_t)layer * n + q) * 8;
+        const cd e[4] = {m.a, m.b, m.c, m.d};
+        for (int k = 0; k < 4; ++k) { d[2 * k] = e[k].real(); d[2 * k + 1] = e[k].imag(); }
+    };
+    // step l: S_l Z_l S_l with S_l = exp[i tau/2 sum (A_l X - B_l h Z)] and
+    // Z_l = exp[-i tau B_l sum J Z Z].  The engine's layer k applies
+    // exp(-i gamma_k H_C) (fields included) and then per-qubit matrices, so
+    // the fields' part F_l = exp(-i tau B_l h Z) of that phase is undone in
+    // the following matrices: Z_l = F_l^{-1} exp(-i tau B_l H_C), and F_l^{-1}
+    // commutes with the phase.  Layer 0: gamma = 0, S_0; layer l + 1: gamma =
+    // tau B_l, S_{l+1} S_l F_l^{-1} (S_nsteps = 1).
+    gamma[0] = 0.0;
+    for (int q = 0; q < n; ++q) put(0, q, nsteps > 0 ? spin(0.5 * tau, A[0], -B[0] * hfield[q]) : id);
+    for (int l = 0; l < nsteps; ++l) {
+        gamma[l + 1] = tau * B[l];
+        for (int q = 0; q < n; ++q) {
+            const M2 Sl = spin(0.5 * tau, A[l], -B[l] * hfield[q]);
+            const M2 Sn = l + 1 < nsteps ? spin(0.5 * tau, A[l + 1], -B[l + 1] * hfield[q]) : id;
+            const double th = tau * B[l] * hfield[q];
+            const M2 Finv{std::polar(1.0, th), 0.0, 0.0, std::polar(1.0, -th)};  // exp(+i tau B h Z)
+            put(l + 1, q, mul(Sn, mul(Sl, Finv)));
+        }
+    }
     return QS_OK;
 }
 

@@ -46,7 +46,8 @@ enum : int {
     T_STORE = 8,      // write the tile back (clear only for the last reverse sweep)
     T_ADJOINT = 16,   // two arrays (psi, lambda), gradient accumulation
     T_ZEXP = 32,      // record <Z_q> of the layer ending at each phase point and at the readout
-    T_TAB = 64        // work queue: the tile needs its cost table (a phase or a readout)
+    T_TAB = 64,       // work queue: the tile needs its cost table (a phase or a readout)
+    T_SU2 = 128       // general single-spin unitaries per layer and qubit instead of x rotations
 };
 
 // Per-layer spin expectations <Z_q> (Sec. III.B.2, Fig. 6): every CTA of a
@@ -62,8 +63,9 @@ constexpr int kZSlots = kMaxRounds + 1;  // records per CTA
 // without a phase) also drops the phase.  Leaner variants keep the
 // instruction footprint of the hot loop small.  ZFULL is FULL with the spin
 // expectations of T_ZEXP sweeps; ZPHASE is PHASE with them (the packed-pair
-// kernel; sweep_kernel runs ZPHASE sweeps as ZFULL).
-enum : int { V_FULL = 0, V_PHASE = 1, V_LEAN = 2, V_ZFULL = 3, V_ZPHASE = 4 };
+// kernel; sweep_kernel runs ZPHASE sweeps as ZFULL).  SU2 is FULL with
+// general per-qubit 2 x 2 unitaries in place of the x rotations.
+enum : int { V_FULL = 0, V_PHASE = 1, V_LEAN = 2, V_ZFULL = 3, V_ZPHASE = 4, V_SU2 = 5 };
 
 struct SweepRound {
     int layer;       // index into the per-layer parameter array
@@ -95,6 +97,7 @@ struct SweepTask {
     const int32_t* tprog;        // tile program of the shape (build_tile_prog)
     double* partials;            // per tile: np doubles
     double* zpart;               // T_ZEXP: per CTA kZSlots * kZQ doubles
+    const double* su2;           // T_SU2: per layer and qubit a 2 x 2 unitary (8 doubles, row major)
     int64_t ntiles;
     int64_t part_base;           // first partial slot of this task
     int n, c, g0, flags;

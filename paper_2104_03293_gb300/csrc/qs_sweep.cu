@@ -11,6 +11,8 @@ int sweep_other(int dtype, int adjoint, int kind, bool grid_only, const SweepLau
                 cudaError_t* status);
 int sweep_zexp(int dtype, int kind, bool grid_only, const SweepLaunch* L, int grid, cudaStream_t st,
                cudaError_t* status);
+int sweep_su2(int dtype, int kind, bool grid_only, const SweepLaunch* L, int grid, cudaStream_t st,
+              cudaError_t* status);
 
 cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st) {
     if (L.total_tiles <= 0) return cudaSuccess;
@@ -20,7 +22,8 @@ cudaError_t launch_sweep(const SweepLaunch& L, int grid, cudaStream_t st) {
     if (L.pairc == 1 && !L.adjoint) return launch_sweep_runs(L, grid, st);
     if (L.pairc) return L.adjoint ? launch_sweep_pair_adj(L, grid, st) : launch_sweep_pair(L, grid, st);
     cudaError_t s = cudaErrorInvalidValue;
-    if (!L.adjoint && (L.variant == V_ZFULL || L.variant == V_ZPHASE)) sweep_zexp(L.dtype, L.kind, false, &L, grid, st, &s);
+    if (!L.adjoint && L.variant == V_SU2) sweep_su2(L.dtype, L.kind, false, &L, grid, st, &s);
+    else if (!L.adjoint && (L.variant == V_ZFULL || L.variant == V_ZPHASE)) sweep_zexp(L.dtype, L.kind, false, &L, grid, st, &s);
     else if (L.dtype == 0 && !L.adjoint) sweep_c64f(L.kind, L.variant, false, &L, grid, st, &s);
     else sweep_other(L.dtype, L.adjoint, L.kind, false, &L, grid, st, &s);
     return s;
@@ -40,6 +43,7 @@ int pair_choice(int dtype, int adjoint, int kind, int c, int variant) {
 }
 
 int sweep_variant(int flags, int nrounds, const SweepRound* rounds) {
+    if (flags & T_SU2) return V_SU2;
     if (flags & T_ZEXP)  // spin expectations: with or without the other fused work
         return (flags & (T_GEN | T_READOUT | T_WRITE_LAM | T_ADJOINT)) ? V_ZFULL : V_ZPHASE;
     if (flags & (T_GEN | T_READOUT | T_WRITE_LAM | T_ADJOINT)) return 0;  // full

@@ -126,6 +126,10 @@ struct TMap {
         const uint32_t cm = (1u << c) - 1u, m1 = (1u << n1) - 1u;
         return (uint64_t)(e & cm) | ((uint64_t)((e >> c) & m1) << g0) | ((uint64_t)(e >> (c + n1)) << g1);
     }
+    // global bit of tile bit tb
+    __device__ __forceinline__ int gbit(int tb) const {
+        return tb < c ? tb : (tb < c + n1 ? g0 + tb - c : g1 + tb - c - n1);
+    }
     // tile bit holding global bit q, or -1 when q lies outside the tile
     __device__ __forceinline__ int tile_bit(int q) const {
         if (q < c) return q;
@@ -502,6 +506,46 @@ struct Sweep {
             }
         });
     }
+    // General single-spin unitaries (the x + z exponentials of Eq. AQA4): the
+    // target qubit q of register bit b gets (a, b) -> (u00 a + u01 b,
+    // u10 a + u11 b) with u = U[8 q ..] (row major, re / im pairs, FP64).
+    template <int g>
+    __device__ static __forceinline__ void rotate_su2(C2 (&v)[NA][NS], const double* __restrict__ U, const TMap& tm,
+                                                      int c) {
+        static_for<0, R>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int tb = reg_bit<g, b>();
+            constexpr int rk = rank_of(K, LK, tb);
+            if constexpr (rk < rot_lo<g>() || rk >= rot_hi<g>()) return;  // not rotated in this layout
+            if (KIND == 1 && tb < c) return;                             // carried bit
+            const double* u = U + 8 * tm.gbit(tb);
+            const Real u0r = (Real)__ldg(u), u0i = (Real)__ldg(u + 1), u1r = (Real)__ldg(u + 2),
+                       u1i = (Real)__ldg(u + 3), u2r = (Real)__ldg(u + 4), u2i = (Real)__ldg(u + 5),
+                       u3r = (Real)__ldg(u + 6), u3i = (Real)__ldg(u + 7);
+#pragma unroll
+            for (int m = 0; m < NS; ++m) {
+                if (m & (1 << b)) continue;
+                const int m2 = m | (1 << b);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const C2 x = v[a][m], y = v[a][m2];
+                    C2 nx, ny;
+                    nx.x = fma_(u0r, x.x, fma_(-u0i, x.y, fma_(u1r, y.x, -u1i * y.y)));
+                    nx.y = fma_(u0r, x.y, fma_(u0i, x.x, fma_(u1r, y.y, u1i * y.x)));
+                    ny.x = fma_(u2r, x.x, fma_(-u2i, x.y, fma_(u3r, y.x, -u3i * y.y)));
+                    ny.y = fma_(u2r, x.y, fma_(u2i, x.x, fma_(u3r, y.y, u3i * y.x)));
+                    v[a][m] = nx;
+                    v[a][m2] = ny;
+                }
+            }
+        });
+    }
+    __device__ static __forceinline__ void rotate_su2_any(int g, C2 (&v)[NA][NS], const double* U, const TMap& tm,
+                                                          int c) {
+        if (g == 0) rotate_su2<0>(v, U, tm, c);
+        else if (G > 1 && g == 1) rotate_su2<(G > 1 ? 1 : 0)>(v, U, tm, c);
+        else if (G > 2) rotate_su2<(G > 2 ? 2 : 0)>(v, U, tm, c);
+    }
     __device__ static __forceinline__ void rotate_any(int g, C2 (&v)[NA][NS], Real w, int c, Real fabs2, Real& fpow,
                                                       Real& gacc) {
         if (g == 0) rotate<0>(v, w, c, fabs2, fpow, gacc);
@@ -612,7 +656,8 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
     using C2 = typename S::C2;
     constexpr int NS = S::NS, NW = S::NW, NSLOT = S::NSLOT;
     constexpr bool kZ = V == V_ZFULL && NA == 1;
-    constexpr bool kGen = V == V_FULL || kZ, kPhase = V != V_LEAN, kRead = V == V_FULL || kZ;
+    constexpr bool kSU2 = V == V_SU2 && NA == 1;  // general single-spin unitaries instead of x rotations
+    constexpr bool kGen = V == V_FULL || kZ || kSU2, kPhase = V != V_LEAN, kRead = V == V_FULL || kZ || kSU2;
     static_assert(KIND != 1 || make_layout(K, R, KIND).regs[0][0] == K - R, "layout 0 holds the top R tile bits");
     extern __shared__ __align__(128) unsigned char smraw[];
     C2* buf = reinterpret_cast<C2*>(smraw);                                      // [NA][2^K]
@@ -794,15 +839,18 @@ __global__ void __launch_bounds__(1 << (K - R), NA == 1 ? 2 : 1)
             if (NA == 2)
                 for (int i = 0; i < rd.r0; ++i) fpow *= fabs2;  // |f|^{2 r0}, no FP64 on the device
             const Real w = (Real)ly.w;
+            const double* U = kSU2 ? T.su2 + (size_t)rd.layer * T.n * 8 : nullptr;
             if (cur == 0) {
                 for (int g = 0; g < ga; ++g) {
                     if (g != cur) { transpose(cur, g); cur = g; }
-                    S::rotate_any(g, v, w, c, fabs2, fpow, gB);
+                    if (kSU2) S::rotate_su2_any(g, v, U, tm, c);
+                    else S::rotate_any(g, v, w, c, fabs2, fpow, gB);
                 }
             } else {
                 for (int g = ga - 1; g >= 0; --g) {
                     if (g != cur) { transpose(cur, g); cur = g; }
-                    S::rotate_any(g, v, w, c, fabs2, fpow, gB);
+                    if (kSU2) S::rotate_su2_any(g, v, U, tm, c);
+                    else S::rotate_any(g, v, w, c, fabs2, fpow, gB);
                 }
             }
             if (kPhase && rd.phase_post) S::phase_any(cur, v, T, tt, tid, ltab, ly.frame, gG);

@@ -64,6 +64,8 @@ _SIGS = {
     "qs_batch_autotune": [_P, _PI, _PI64, _PD],
     "qs_grad": [_P, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "qs_evolve_zexp": [_P, _I, _PD, _PD, _PD],
+    "qs_evolve_su2": [_P, _I, _PD, _PD],
+    "qs_qsds_layers": [_I, _I, _D, _PD, _PD, _PD, _PD, _PD],
     "qs_set_adjoint_buffer": [_P, _P, ctypes.c_size_t],
     "qs_copy_state": [_P, _P, ctypes.c_size_t],
     "qs_state_ptr": [_P, ctypes.POINTER(_P), _PI],
@@ -237,6 +239,14 @@ class State:
         _check(lib().qs_evolve_zexp(self._h, int(g.size), _dptr(g), _dptr(b), _dptr(out)))
         return out
 
+    def evolve_su2(self, gamma, u):
+        """Layers exp(-i gamma_k H_C) then per-qubit 2 x 2 matrices u[k, i]
+        (complex array [p, n, 2, 2]) from |+>^n."""
+        g = _f64(np.atleast_1d(gamma))
+        uu = np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(g.size, self.n, 2, 2))
+        flat = np.ascontiguousarray(uu.reshape(-1).view(np.float64))
+        _check(lib().qs_evolve_su2(self._h, int(g.size), _dptr(g), _dptr(flat)))
+
     def readout(self):
         E, P, N = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().qs_readout(self._h, ctypes.byref(E), ctypes.byref(P), ctypes.byref(N)))
@@ -381,6 +391,17 @@ def aqa_angles(tau: float, s) -> tuple:
     g, b = np.zeros_like(s), np.zeros_like(s)
     _check(lib().qs_aqa_angles(int(s.size), float(tau), _dptr(s), _dptr(g), _dptr(b)))
     return g, b
+
+
+def qsds_layers(n: int, tau: float, A, B, hfield):
+    """(gamma [nsteps + 1], u [nsteps + 1, n, 2, 2]) reproducing the product
+    formula of Eq. (AQA4) with evolve_su2 (host)."""
+    a, b, h = _f64(A), _f64(B), _f64(hfield)
+    assert a.shape == b.shape and h.shape == (n,)
+    g = np.zeros(a.size + 1)
+    flat = np.zeros((a.size + 1) * n * 8)
+    _check(lib().qs_qsds_layers(int(n), int(a.size), float(tau), _dptr(a), _dptr(b), _dptr(h), _dptr(g), _dptr(flat)))
+    return g, flat.view(np.complex128).reshape(a.size + 1, n, 2, 2)
 
 
 def aqa_angles_2nd(tau: float, s) -> tuple:

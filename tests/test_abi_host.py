@@ -140,3 +140,29 @@ def test_binding_checks_the_lengths_the_c_side_reads(lib):
     assert g.shape == b.shape == (1,)
     with pytest.raises(ValueError):
         qs.State(4, dtype="c32")
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_qsds_layers_reproduce_the_product_formula(lib, seed):
+    """qs_qsds_layers: applying its layers with the oracle's own gates (the
+    phase exp(-i gamma H_C) with the fields, then each qubit's 2 x 2 matrix)
+    gives the oracle's step-by-step Eq. (AQA4) state; every matrix is
+    unitary; the layer count is nsteps + 1."""
+    from paper_2104_03293_gb300 import instances as I
+    inst = I.erdos_renyi_ising(7, 40 + seed)
+    nsteps, tau = 6, 0.5
+    s = (np.arange(nsteps) + 0.5) / nsteps
+    A, B = 1.0 - s, s
+    g, u = qs.qsds_layers(inst.n, tau, A, B, inst.h)
+    assert g.shape == (nsteps + 1,) and u.shape == (nsteps + 1, inst.n, 2, 2)
+    for m in u.reshape(-1, 2, 2):
+        assert np.max(np.abs(m.conj().T @ m - np.eye(2))) <= 1e-14
+    psi = oracle.evolve(inst, [0.0], [0.0])  # |+>^n
+    for k in range(nsteps + 1):
+        psi = oracle.evolve(inst, [g[k]], [0.0], psi=psi)
+        for q in range(inst.n):
+            oracle.gate_u(inst.n, psi, q, u[k, q])
+    want = oracle.qsds_evolve(inst, tau, A, B)
+    assert np.max(np.abs(psi - want)) <= 1e-12
+    with pytest.raises(qs.QSError):
+        qs.qsds_layers(0, tau, A, B, inst.h[:0])
