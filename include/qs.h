@@ -211,7 +211,7 @@ int qs_enumerate_noalloc(int n, const double* hfield, int n_edges, const int32_t
  * Errors: QS_EINVAL. */
 int qs_set_shape_rule(qs_handle h, int runs_a, int split);
 
-/* Plan rule of the handle: five ints
+/* Plan rule of the handle: QS_PLAN_RULE_INTS ints
  *   [0] runs_a, [1] split   as qs_set_shape_rule;
  *   [2] cmin         carried low bits of the strided shapes: 2 (rows of 32
  *                    bytes, 11 targets per shape) or 3 (64-byte rows, 10
@@ -219,10 +219,19 @@ int qs_set_shape_rule(qs_handle h, int runs_a, int split);
  *   [3] ctas_per_sm  persistent CTAs per SM of the sweep kernels (0: as many
  *                    as fit);
  *   [4] pair_cluster 4: the strided packed-pair sweeps run in 4-CTA
- *                    clusters that fetch shared HBM lines once; 1: without.
- * Every rule gives the same results up to rounding order.  qs_set_plan_rule
- * re-plans the current Ising cost when the shape fields change.  Errors:
- * QS_EINVAL. */
+ *                    clusters that fetch shared HBM lines once; 1: without;
+ *   [5] pair_tma     1: the strided packed-pair forward sweeps load each
+ *                    tile with two tensor-map copies (TMA) issued by one
+ *                    thread; 0: with per-thread 16-byte cp.async copies
+ *                    (the tensor-map copies fall back to these where a
+ *                    shape does not fit a five-dimensional box);
+ *   [6] pair_l2      L2 fetch size of the strided packed-pair tile loads
+ *                    (forward and reverse sweeps): 0 the default, 1 128
+ *                    bytes, 2 256 bytes.
+ * Every rule gives the same results up to rounding order (the load fields
+ * give bit-identical states).  qs_set_plan_rule re-plans the current Ising
+ * cost when the shape fields change.  Errors: QS_EINVAL. */
+#define QS_PLAN_RULE_INTS 7
 int qs_set_plan_rule(qs_handle h, const int* rule);
 int qs_get_plan_rule(qs_handle h, int* rule);
 
@@ -232,11 +241,13 @@ int qs_get_plan_rule(qs_handle h, int* rule);
  * shape A; for complex64 states of 24 qubits and more the run-structured A
  * with split bits 20, 22 and 24; each with cmin 2 and 3), then, for the best
  * shapes, one CTA per SM fewer than fit and (complex64) the strided sweeps
- * without clusters.  Reports the measured candidates (up to max_cand rules
- * of five ints in cand_rules with their times in cand_ms, the count in
- * ncand) and the kept rule (best_rule, five ints) with its time; any output
- * may be NULL when max_cand = 0.  Overwrites the state.  Call after
- * qs_set_ising.  Errors: QS_ESTATE, QS_EINVAL, QS_ECUDA. */
+ * without clusters, then (complex64) the strided tile loads: cp.async with
+ * 128- or 256-byte L2 fetches, tensor-map copies with the default or 256-
+ * byte fetches.  Reports the measured candidates (up to max_cand rules of
+ * QS_PLAN_RULE_INTS ints in cand_rules with their times in cand_ms, the
+ * count in ncand) and the kept rule (best_rule, QS_PLAN_RULE_INTS ints) with
+ * its time; any output may be NULL when max_cand = 0.  Overwrites the
+ * state.  Call after qs_set_ising.  Errors: QS_ESTATE, QS_EINVAL, QS_ECUDA. */
 int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand_rules, double* cand_ms,
                    int* best_rule, double* best_ms);
 
@@ -289,6 +300,20 @@ int qs_plan_sweeps(int n, int dtype, int p, int* tile_shapes, int* sweeps);
  * target runs [g0, g0 + n1) and [g1, g1 + K - c - n1).  Returns QS_EINVAL
  * when k is past the last shape. */
 int qs_plan_shape(int n, int dtype, int k, int* kind, int* K, int* c, int* g0, int* n1, int* g1);
+
+/* Tensor-map view of the tiles of a strided complex64 shape (K = 13 tile
+ * bits, c = 2 or 3 carried bits, target runs [g0, g0 + n1) and [g1, g1 +
+ * 13 - c - n1) of an n-qubit state) loaded for a first read into register
+ * layout g (0 or 1) of the packed-pair forward sweep (host only; the
+ * plan rule's pair_tma).  Outputs: rank (at most 5) dimensions, dimension d
+ * covering global index bits [start[d], start[d] + width[d]) of which the
+ * box holds the lowest box[d] (dimension 0 starts at bit 0), in the box's
+ * shared-memory order; kbit is the global bit of the pack bit, one box
+ * copy per value; landing[tb] (13 ints) is the shared-memory position bit
+ * of tile bit tb.  Every array has room for 5 (landing: 13) ints.
+ * Returns QS_EINVAL for a shape that does not fit such a box. */
+int qs_pair_tile_map(int n, int c, int g0, int n1, int g1, int g, int* rank, int* kbit, int* start, int* width,
+                     int* box, int* landing);
 
 /* Number of kernels this library has launched in this process so far (all
  * handles and batches).  For accounting in benchmarks. */

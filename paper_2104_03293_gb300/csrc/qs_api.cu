@@ -9,6 +9,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "../../include/qs.h"
 #include "qs_api_common.h"
@@ -231,6 +232,8 @@ struct qs_state {
     ShapeRule rule;                      // tile-shape plan (qs_set_shape_rule / qs_autotune)
     int ctas_per_sm = 0;                 // launch rule: persistent CTAs per SM (0 = as many as fit)
     int pair_cluster = 4;                // launch rule: strided packed-pair sweeps in 4-CTA clusters or not
+    int pair_tma = 0;                    // launch rule: strided packed-pair forward tiles by tensor-map copies
+    int pair_l2 = 0;                     // launch rule: L2 fetch size of those tile loads (0 default, 1 128 B, 2 256 B)
     int sms = 0;                         // multiprocessors of the device
     std::vector<double> ising_h, ising_J;  // the last qs_set_ising input, to re-plan
     std::vector<int32_t> ising_e;
@@ -347,6 +350,61 @@ int qs_set_ising(qs_handle h, const double* hfield, int n_edges, const int32_t* 
     return QS_OK;
 }
 
+static_assert(kPlanRuleInts == QS_PLAN_RULE_INTS, "plan rule length");
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link-time
+// dependence on libcuda); null when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && p)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tile loads of a strided packed-pair forward sweep over psi whose tiles are
+// first read into layout g: tensor-map copies when the rule asks for them
+// and the shape fits (pair_tma_dims), else cp.async; the L2 fetch size in
+// both cases.
+static PairLoad make_pair_load(qs_handle h, const Shape& s, void* psi, int g) {
+    PairLoad L;
+    std::memset(&L, 0, sizeof L);
+    L.l2 = h->pair_l2;
+    PairTmaDims d;
+    auto enc = h->pair_tma ? tensor_map_encoder() : nullptr;
+    if (!enc || !pair_tma_dims(s, h->nphys, g, d)) return L;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], es[5] = {1, 1, 1, 1, 1};
+    for (int i = 0; i < d.rank; ++i) {
+        // dimension 0 in floats (two per amplitude), the others in amplitudes
+        dims[i] = (cuuint64_t)1 << (d.width[i] + (i == 0 ? 1 : 0));
+        box[i] = 1u << (d.box[i] + (i == 0 ? 1 : 0));
+        if (i > 0) strides[i - 1] = (cuuint64_t)8 << d.start[i];
+        L.lo[i] = d.start[i];
+        L.nb[i] = d.width[i];
+    }
+    const CUtensorMapL2promotion promo = h->pair_l2 == 2   ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                                         : h->pair_l2 == 1 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                           : CU_TENSOR_MAP_L2_PROMOTION_NONE;
+    const CUresult r = enc(&L.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)d.rank, psi, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return L;
+    L.rank = d.rank;
+    L.kbit = d.kbit;
+    L.tma = 1;
+    return L;
+}
+
 // Rebuild the instance's shapes and cost programs under h->rule.
 static int replan(qs_handle h) {
     if (!h->inst.valid) return QS_OK;
@@ -371,15 +429,19 @@ int qs_set_shape_rule(qs_handle h, int runs_a, int split) {
 int qs_set_plan_rule(qs_handle h, const int* rule) {
     if (int rc = check_handle(h)) return rc;
     if (!rule) return set_error(QS_EINVAL, "qs_set_plan_rule: rule is NULL");
-    const int runs_a = rule[0], split = rule[1], cmin = rule[2], cps = rule[3], cl = rule[4];
+    const int runs_a = rule[0], split = rule[1], cmin = rule[2], cps = rule[3], cl = rule[4], tma = rule[5],
+              l2 = rule[6];
     if (runs_a < -1 || runs_a > 1 || split < -1 || split >= h->nphys + 1 || !(cmin == -1 || cmin == 2 || cmin == 3) ||
-        cps < 0 || cps > 32 || !(cl == 1 || cl == 4))
+        cps < 0 || cps > 32 || !(cl == 1 || cl == 4) || tma < 0 || tma > 1 || l2 < 0 || l2 > 2)
         return set_error(QS_EINVAL, "qs_set_plan_rule: runs_a in {-1, 0, 1}, split in [-1, n], cmin in {-1, 2, 3}, "
-                                    "ctas_per_sm in [0, 32], pair_cluster in {1, 4}");
+                                    "ctas_per_sm in [0, 32], pair_cluster in {1, 4}, pair_tma in {0, 1}, pair_l2 in "
+                                    "{0, 1, 2}");
     const bool reshape = runs_a != h->rule.runs_a || split != h->rule.split || cmin != h->rule.cmin;
     h->rule = ShapeRule{runs_a, split, cmin};
     h->ctas_per_sm = cps;
     h->pair_cluster = cl;
+    h->pair_tma = tma;
+    h->pair_l2 = l2;
     return reshape ? replan(h) : QS_OK;
 }
 
@@ -391,6 +453,8 @@ int qs_get_plan_rule(qs_handle h, int* rule) {
     rule[2] = h->rule.cmin;
     rule[3] = h->ctas_per_sm;
     rule[4] = h->pair_cluster;
+    rule[5] = h->pair_tma;
+    rule[6] = h->pair_l2;
     return QS_OK;
 }
 
@@ -420,26 +484,39 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
     if (!h->inst.valid) return set_error(QS_ESTATE, "qs_autotune: call qs_set_ising first");
     if (p_trial < 1 || p_trial > 64) return set_error(QS_EINVAL, "qs_autotune: p_trial outside [1, 64]");
     if (max_cand > 0 && (!cand_rules || !cand_ms)) return set_error(QS_EINVAL, "qs_autotune: NULL candidate arrays");
-    struct Cand { ShapeRule r; int cps, cl; double ms; };
+    struct Cand {
+        ShapeRule r;
+        int cps, cl, tma, l2;
+        double ms;
+    };
     std::vector<Cand> done;
     std::vector<double> g(p_trial, 0.3), b(p_trial, 0.7);
-    const ShapeRule keep = h->rule;
-    const int keep_cps = h->ctas_per_sm, keep_cl = h->pair_cluster;
+    const Cand keep{h->rule, h->ctas_per_sm, h->pair_cluster, h->pair_tma, h->pair_l2, 0.0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     if (ce != cudaSuccess) return cuda_error(ce, "qs_autotune: events");
     int rc = QS_OK;
-    auto measure = [&](const ShapeRule& r, int cps, int cl) -> double {
-        const bool reshape = r.runs_a != h->rule.runs_a || r.split != h->rule.split || r.cmin != h->rule.cmin;
-        h->rule = r;
-        h->ctas_per_sm = cps;
-        h->pair_cluster = cl;
-        double ms = 1e300;
-        if (reshape && (rc = replan(h))) return ms;
-        if ((rc = time_evolve(h, p_trial, g.data(), b.data(), e0, e1, &ms))) return 1e300;
-        done.push_back(Cand{r, cps, cl, ms});
-        return ms;
+    auto apply = [&](const Cand& c) {
+        h->rule = c.r;
+        h->ctas_per_sm = c.cps;
+        h->pair_cluster = c.cl;
+        h->pair_tma = c.tma;
+        h->pair_l2 = c.l2;
+    };
+    double best = 1e300;
+    Cand pick{ShapeRule{0, page_bit_for(h->dtype), -1}, 0, 4, 0, 0, 1e300};
+    auto measure = [&](Cand c) {
+        const bool reshape = c.r.runs_a != h->rule.runs_a || c.r.split != h->rule.split || c.r.cmin != h->rule.cmin;
+        apply(c);
+        c.ms = 1e300;
+        if (reshape && (rc = replan(h))) return;
+        if ((rc = time_evolve(h, p_trial, g.data(), b.data(), e0, e1, &c.ms))) return;
+        done.push_back(c);
+        if (c.ms < best) {
+            best = c.ms;
+            pick = c;
+        }
     };
     // stage 1, tile shapes: contiguous shape A with the page-bit split and,
     // for complex64 states of 24 qubits and more, the run-structured A with
@@ -449,12 +526,9 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
         for (int sp : {20, 22, 24}) shapes.push_back(ShapeRule{1, sp, -1});
     const size_t ns = shapes.size();
     for (size_t i = 0; i < ns; ++i) shapes.push_back(ShapeRule{shapes[i].runs_a, shapes[i].split, 3});
-    double best = 1e300;
-    Cand pick{shapes[0], 0, 4, 1e300};
     for (const ShapeRule& r : shapes) {
-        const double ms = measure(r, 0, 4);
+        measure(Cand{r, 0, 4, 0, 0, 0.0});
         if (rc) break;
-        if (ms < best) { best = ms; pick = Cand{r, 0, 4, ms}; }
     }
     // stage 2, launch: one CTA per SM fewer than fit, and (complex64) the
     // strided packed-pair sweeps without their 4-CTA clusters
@@ -466,42 +540,44 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
         std::vector<std::pair<int, int>> launch;
         if (per_sm > 1) launch.push_back({per_sm - 1, 4});
         if (h->dtype == QS_C64) launch.push_back({0, 1});
+        const Cand base = pick;
         for (auto [cps, cl] : launch) {
-            const double ms = measure(pick.r, cps, cl);
+            measure(Cand{base.r, cps, cl, 0, 0, 0.0});
             if (rc) break;
-            if (ms < best) { best = ms; pick = Cand{pick.r, cps, cl, ms}; }
+        }
+    }
+    // stage 3 (complex64), the strided packed-pair tile loads: the copies'
+    // L2 fetch size (128 or 256 bytes), and tensor-map copies
+    if (!rc && h->dtype == QS_C64) {
+        const Cand base = pick;
+        const int loads[4][2] = {{0, 1}, {0, 2}, {1, 0}, {1, 2}};
+        for (const auto& ld : loads) {
+            measure(Cand{base.r, base.cps, base.cl, ld[0], ld[1], 0.0});
+            if (rc) break;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) {
-        h->rule = keep;
-        h->ctas_per_sm = keep_cps;
-        h->pair_cluster = keep_cl;
-    } else {
-        h->rule = pick.r;
-        h->ctas_per_sm = pick.cps;
-        h->pair_cluster = pick.cl;
-    }
+    apply(rc ? keep : pick);
     if (int rc2 = replan(h)) return rc ? rc : rc2;
     if (rc) return rc;
     if (ncand) *ncand = (int)done.size();
     for (int i = 0; i < (int)done.size() && i < max_cand; ++i) {
         const Cand& c = done[i];
-        const int v[5] = {c.r.runs_a, c.r.split, c.r.cmin, c.cps, c.cl};
-        for (int k = 0; k < 5; ++k) cand_rules[5 * i + k] = v[k];
+        const int v[kPlanRuleInts] = {c.r.runs_a, c.r.split, c.r.cmin, c.cps, c.cl, c.tma, c.l2};
+        for (int k = 0; k < kPlanRuleInts; ++k) cand_rules[kPlanRuleInts * i + k] = v[k];
         cand_ms[i] = c.ms;
     }
     if (best_rule) {
-        const int v[5] = {pick.r.runs_a, pick.r.split, pick.r.cmin, pick.cps, pick.cl};
-        for (int k = 0; k < 5; ++k) best_rule[k] = v[k];
+        const int v[kPlanRuleInts] = {pick.r.runs_a, pick.r.split, pick.r.cmin, pick.cps, pick.cl, pick.tma, pick.l2};
+        for (int k = 0; k < kPlanRuleInts; ++k) best_rule[k] = v[k];
     }
     if (best_ms) *best_ms = best;
     return QS_OK;
 }
 
 int qs_autotune(qs_handle h, int p_trial, int* runs_a, int* split, double* best_ms) {
-    int rule[5];
+    int rule[kPlanRuleInts];
     if (int rc = qs_autotune_ex(h, p_trial, 0, nullptr, nullptr, nullptr, rule, best_ms)) return rc;
     if (runs_a) *runs_a = rule[0];
     if (split) *split = rule[1];
@@ -723,6 +799,11 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
         L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
         L.pq = &I.pair_q[fwd[i].shape];
         L.cluster = h->pair_cluster;
+        PairLoad pl;
+        if (L.pairc >= 2) {
+            pl = make_pair_load(h, sh, h->psi, fwd[i].nr & 1);
+            L.load = &pl;
+        }
         e = launch_sweep(L, forward_grid(h, L), h->st);
         if (e != cudaSuccess) return cuda_error(e, "sweep launch");
         if (zred_cnt[i]) {
@@ -738,6 +819,7 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
                       reinterpret_cast<const int64_t*>(dblob + rev_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 1, sh.kind, sh.c, 0);
         L.paq = &I.pair_adj_q[rev[i].shape];
+        L.l2 = h->pair_l2;
         e = launch_sweep(L, grid_for(h, L.pairc ? 3 : L.kind, 1), h->st);
         if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
         if (red_cnt[i]) {
@@ -1045,6 +1127,37 @@ int qs_plan_shape(int n, int dtype, int k, int* kind, int* K, int* c, int* g0, i
     if (g0) *g0 = s.g0;
     if (n1) *n1 = s.n1;
     if (g1) *g1 = s.g1;
+    return QS_OK;
+}
+
+int qs_pair_tile_map(int n, int c, int g0, int n1, int g1, int g, int* rank, int* kbit, int* start, int* width,
+                     int* box, int* landing) {
+    if (!rank || !kbit || !start || !width || !box || !landing)
+        return set_error(QS_EINVAL, "qs_pair_tile_map: NULL output");
+    const int nt = kPairK - c;
+    const bool runs_ok = c >= 0 && n1 >= 0 && n1 <= nt && g0 >= c && g1 >= c && n <= QS_MAX_QUBITS_C64 &&
+                         g0 + n1 <= n && g1 + (nt - n1) <= n && (n1 == 0 || g1 >= g0 + n1 || g1 + nt - n1 <= g0);
+    if (!runs_ok) return set_error(QS_EINVAL, "qs_pair_tile_map: not a strided shape of %d qubits", n);
+    Shape s;
+    s.K = kPairK;
+    s.c = c;
+    s.g0 = g0;
+    s.nt = nt;
+    s.kind = 1;
+    s.n1 = n1;
+    s.g1 = g1;
+    s.ntiles = (int64_t)1 << (n - kPairK);
+    PairTmaDims d;
+    if (!pair_tma_dims(s, n, g, d)) return set_error(QS_EINVAL, "qs_pair_tile_map: the shape does not fit a box");
+    *rank = d.rank;
+    *kbit = d.kbit;
+    for (int i = 0; i < 5; ++i) {
+        start[i] = i < d.rank ? d.start[i] : 0;
+        width[i] = i < d.rank ? d.width[i] : 0;
+        box[i] = i < d.rank ? d.box[i] : 0;
+    }
+    const PairTmaPos tp = pair_tma_pos(c, g);
+    for (int tb = 0; tb < kPairK; ++tb) landing[tb] = tp.pos[tb];
     return QS_OK;
 }
 

@@ -154,6 +154,46 @@ QS_PHD constexpr PairRunsLayout pair_runs_layout() {
     return t;
 }
 
+// Landing order of a strided tile loaded by tensor-map copies (the TMA
+// variant of the packed-pair forward sweep), for a tile first read into
+// layout g.  pos[tb] is the shared-memory position bit (in 8-byte
+// amplitudes) of tile bit tb; the pack bit sits on position 12, so the tile
+// arrives as two box copies of 2^12 amplitudes, one per value of the pack
+// bit.  A box lays its dimensions out in the order of their position bits,
+// and each dimension is a run of consecutive global bits, so the host
+// derives the tensor map from this table and the tile's shape.  Positions
+// 0-3 hold the four lane bits of a half-warp of layout g (tile bits 0, 1
+// and, for C = 2, 3, 4 in layout 0 or 8, 9 in layout 1; for C = 3, bit 2
+// and 4 or 8), so the 8-byte reads into layout g hit 16 distinct bank pairs
+// without a swizzle (checked on the host by the test-suite).  The copies are
+// unswizzled: a swizzle span above the 32- or 64-byte box rows would space
+// the rows out to the span.
+struct PairTmaPos {
+    int pos[13];
+};
+
+QS_PHD constexpr PairTmaPos pair_tma_pos(int C, int g) {
+    PairTmaPos t{};
+    // landing order: the carried bits, then the half-warp's other lane
+    // bits with the run they start, then the remaining tile bits in order
+    int order[12] = {};
+    int k = 0;
+    for (int b = 0; b < C; ++b) order[k++] = b;
+    const int first = C == 2 ? (g == 0 ? 3 : 8) : (g == 0 ? 4 : 8);
+    for (int b = first; b < 13; ++b) order[k++] = b;
+    for (int b = C + 1; b < first; ++b) order[k++] = b;
+    for (int q = 0; q < 12; ++q) t.pos[order[q]] = q;
+    t.pos[C] = 12;  // the pack bit: which box copy
+    return t;
+}
+
+// Landing position of tile element e (a bit permutation: linear over XOR).
+QS_PHD constexpr unsigned pair_tma_land(int C, int g, unsigned e) {
+    unsigned p = 0;
+    for (int b = 0; b < 13; ++b) p |= ((e >> b) & 1u) << pair_tma_pos(C, g).pos[b];
+    return p;
+}
+
 // Pair unit of tile element e: e with the pack bit P removed.
 QS_PHD constexpr unsigned pair_unit(unsigned e, int P) {
     return (e & ((1u << P) - 1u)) | ((e >> (P + 1)) << P);

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "qs_layout.h"
+#include "qs_pair.h"
 #include "qs_plan.h"
 
 namespace qs {
@@ -207,6 +208,43 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, Sh
     for (auto& s : v)
         if (s.kind == 1 && s.g0 + s.n1 == s.g1) { s.n1 = 0; s.g1 = s.g0; }
     return v;
+}
+
+bool pair_tma_dims(const Shape& s, int nphys, int g, PairTmaDims& d) {
+    if (s.kind != 1 || s.K != kPairK || !pair_c_ok(s.c) || (g != 0 && g != 1)) return false;
+    const PairTmaPos tp = pair_tma_pos(s.c, g);
+    int at[kPairK];  // tile bit on each landing position
+    for (int tb = 0; tb < kPairK; ++tb) at[tp.pos[tb]] = tb;
+    // positions 0..11 in order: a new dimension wherever the global bit of
+    // the next position does not follow the previous one, or the box of the
+    // current one is full (256 elements; dimension 0 counts floats)
+    d = PairTmaDims{};
+    int prev = -2;
+    for (int q = 0; q + 1 < kPairK; ++q) {
+        const int g = shape_bit(s, at[q]);
+        if (d.rank > 0 && g == prev + 1 && d.box[d.rank - 1] < (d.rank == 1 ? 7 : 8)) {
+            d.box[d.rank - 1]++;
+        } else {
+            if (d.rank == 5) return false;
+            d.start[d.rank] = g;
+            d.box[d.rank] = 1;
+            d.rank++;
+        }
+        prev = g;
+    }
+    d.kbit = shape_bit(s, at[kPairK - 1]);
+    if (d.start[0] != 0) return false;
+    // each dimension reaches up to the next dimension's first bit
+    for (int i = 0; i < d.rank; ++i) {
+        int hi = nphys;
+        for (int j = 0; j < d.rank; ++j)
+            if (d.start[j] > d.start[i]) hi = std::min(hi, d.start[j]);
+        d.width[i] = hi - d.start[i];
+        // box limits: 256 elements (dimension 0 counts floats, two per amplitude)
+        if (d.box[i] > d.width[i] || d.box[i] + (i == 0 ? 1 : 0) > 8 || d.width[i] + (i == 0 ? 1 : 0) > 32)
+            return false;
+    }
+    return true;
 }
 
 void shape_regq(const Shape& s, int R, int g, int* regq) {

@@ -69,6 +69,20 @@ struct ShapeRule {
     int cmin = -1;  // carried low bits of the strided shapes (2 or 3; -1 = the kernel default, 2)
 };
 std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, ShapeRule rule = ShapeRule{});
+
+// Tensor-map view of a strided packed-pair tile (complex64, K = 13, c = 2 or
+// 3) in the landing order pair_tma_pos(c, g) of a tile first read into
+// layout g: dimension d covers global index
+// bits [start[d], start[d] + width[d]), of which the box holds the lowest
+// box[d]; dimension 0 starts at bit 0 (the carried run).  Every global bit
+// belongs to one dimension: bits that are neither box bits nor the pack bit
+// (global bit kbit) are the tile index, set by the copy's coordinates.
+// False when the shape does not fit five dimensions in that order.
+struct PairTmaDims {
+    int rank = 0, kbit = 0;
+    int start[5] = {}, width[5] = {}, box[5] = {};
+};
+bool pair_tma_dims(const Shape& s, int nphys, int g, PairTmaDims& d);
 void shape_regq(const Shape& s, int R, int g, int* regq);
 int num_layouts(const Shape& s, int R);
 std::vector<PlanSweep> plan_forward(int S, int p, bool gen);

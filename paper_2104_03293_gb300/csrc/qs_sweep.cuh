@@ -301,6 +301,65 @@ struct SlotCost {
     __device__ __forceinline__ int tidx(int m, int top) const { return clamp_tab(idx(m), top); }
 };
 
+// Phase of a thread's 64 amplitudes held as 32 packed pairs (X[j] = the real
+// parts, Y[j] = the imaginary parts of slots 2j and 2j + 1; slot bit 0 is the
+// pack bit, slot bits 1..5 are the pair-index bits), layout Map (slot(b),
+// thr(t) as in SlotCost::init_tile), layout program lp, intra-register
+// couplings q (compile-time indexed; kernel parameters).  The cost of slot m
+// is base - sum over the set bits b of m of f2[b], plus q[m]: base = the
+// cost with every slot spin up (the tile constant, this thread's terms and
+// every slot bit's term fb, less cost_lo) and f2[b] = 2 fb[b].  The slots
+// are walked in four Gray-code chains (slot bits 4, 5 fixed per chain), one
+// add per slot, which keeps eight values live instead of two 8-entry
+// partial-sum tables.
+template <class Map, int NTB>
+__device__ __forceinline__ void pair_phase(float2 (&X)[32], float2 (&Y)[32], const int32_t* __restrict__ lp,
+                                           const TileTab& tt, uint32_t tid, int frame, int cost_lo,
+                                           const float2* __restrict__ tab, int top, const int32_t (&q)[64]) {
+    const int sg = frame ? -1 : 1;
+    const int4* tr = reinterpret_cast<const int4*>(lp + 64) + 2 * tid;
+    const int4 ta = __ldg(tr), tb4 = __ldg(tr + 1);
+    const int hrt[6] = {ta.y, ta.z, ta.w, tb4.x, tb4.y, tb4.z};
+    int base = sg * tt.kf + tt.kc + ta.x - cost_lo;
+    static_for<0, NTB>([&](auto jc) {
+        constexpr int t = decltype(jc)::value;
+        constexpr int tb = Map::thr(t);
+        const int v = sg * tt.H[tb] + tt.D[tb];
+        base += ((tid >> t) & 1u) ? -v : v;
+    });
+    int f2[6];
+    static_for<0, 6>([&](auto bc) {
+        constexpr int bb = decltype(bc)::value;
+        constexpr int tb = Map::slot(bb);
+        const int fb = sg * tt.H[tb] + tt.D[tb] + hrt[bb];
+        base += fb;
+        f2[bb] = 2 * fb;
+    });
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        int run = base - ((ch & 1) ? f2[4] : 0) - ((ch & 2) ? f2[5] : 0);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int gc = i ^ (i >> 1);
+            if (i > 0) {
+                const int bb = __ffs(i) - 1;  // the bit that flips at step i
+                run += ((gc >> bb) & 1) ? -f2[bb] : f2[bb];
+            }
+            const int m = (ch << 4) | gc, j = m >> 1;
+            const float2 f = tab[SlotCost<6>::clamp_tab(run + q[m], top)];
+            if (m & 1) {
+                const float br = X[j].y, bi = Y[j].y;
+                X[j].y = fmaf(br, f.x, -bi * f.y);
+                Y[j].y = fmaf(br, f.y, bi * f.x);
+            } else {
+                const float ar = X[j].x, ai = Y[j].x;
+                X[j].x = fmaf(ar, f.x, -ai * f.y);
+                Y[j].x = fmaf(ar, f.y, ai * f.x);
+            }
+        }
+    }
+}
+
 // Warp-level sum, lane 0 stores into red[warp * nslots + slot].
 __device__ __forceinline__ void warp_sum_to(double v, double* red, int slot, int nslots) {
 #pragma unroll

@@ -8,6 +8,8 @@
 // after the current tile's last shared-memory read.  The difference is the
 // register format: pairs split by component and updated with packed f32x2
 // FMAs (fma.rn.f32x2), transposes as 16-byte pair moves.
+#include <cstring>
+
 #include "qs_pair.h"
 #include "qs_sweep.cuh"
 
@@ -116,6 +118,27 @@ struct PairSweep {
         }
     }
 
+    // from a tile landed by the two tensor-map copies (pair_tma_land order
+    // for layout g) into layout g; the landing map is linear over XOR, so the
+    // thread's part is formed once and each slot's part is a constant
+    template <int g>
+    __device__ static __forceinline__ void lds_tma(const float2* src, float2 (&X)[NJ], float2 (&Y)[NJ],
+                                                   uint32_t tid) {
+        uint32_t lt = 0;
+        static_for<0, 7>([&](auto tc) {
+            constexpr int t = decltype(tc)::value;
+            constexpr uint32_t l = pair_tma_land(C, g, 1u << tb<g, t>());
+            lt ^= ((tid >> t) & 1u) ? l : 0u;
+        });
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const float2 a = src[lt ^ pair_tma_land(C, g, e_slot<g>(j))];
+            const float2 b = src[lt ^ pair_tma_land(C, g, e_slot<g>(j) | (1u << P))];
+            X[j] = make_float2(a.x, b.x);
+            Y[j] = make_float2(a.y, b.y);
+        }
+    }
+
     // ---- rotations: a' = a + w (-i b), b' = b + w (-i a) ----------------------
     template <int g>
     __device__ static __forceinline__ void rotate(float2 (&X)[NJ], float2 (&Y)[NJ], float w) {
@@ -168,23 +191,52 @@ struct PairSweep {
     __device__ static __forceinline__ void phase(float2 (&X)[NJ], float2 (&Y)[NJ], const SweepTask& T,
                                                  const TileTab& tt, uint32_t tid, const float2* __restrict__ tab,
                                                  int frame, const PairQ& pq) {
-        SlotCost<6> sc;
-        sc.template init_tile<Map<g>, 7>(tt, T.cprog[g], tid, frame, T.cost_lo);
-        const int top = T.tab_stride - 1;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int ia = SlotCost<6>::clamp_tab(sc.idx_noq(2 * j) + pq.q[g][2 * j], top);
-            const int ib = SlotCost<6>::clamp_tab(sc.idx_noq(2 * j + 1) + pq.q[g][2 * j + 1], top);
-            const float2 fa = tab[ia];
-            const float2 fb = tab[ib];
-            const float ar = X[j].x, br = X[j].y, ai = Y[j].x, bi = Y[j].y;
-            X[j] = make_float2(fmaf(ar, fa.x, -ai * fa.y), fmaf(br, fb.x, -bi * fb.y));
-            Y[j] = make_float2(fmaf(ar, fa.y, ai * fa.x), fmaf(br, fb.y, bi * fb.x));
-        }
+        pair_phase<Map<g>, 7>(X, Y, T.cprog[g], tt, tid, frame, T.cost_lo, tab, T.tab_stride - 1, pq.q[g]);
     }
 };
 
 }  // namespace
+
+// The two tensor-map copies of the tile whose base index (tile bits clear)
+// is base into dst (one per value of the pack bit, 2^12 amplitudes each),
+// completion on the barrier.  Coordinates: per dimension the index bits it
+// spans; dimension 0 counts floats.
+__device__ __forceinline__ void tma_load_tile(unsigned char* dst, const PairLoad& tm, uint64_t base, uint64_t* bar) {
+    const uint64_t mp = reinterpret_cast<uint64_t>(&tm.map);
+    const uint32_t mb = smem_u32(bar);
+    const int rank = tm.rank;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint64_t bk = base | ((uint64_t)k << tm.kbit);
+        const uint32_t d = smem_u32(dst + (size_t)k * 32768);
+        const int c0 = 2 * (int)((bk >> tm.lo[0]) & ((1ull << tm.nb[0]) - 1ull));
+        const int c1 = (int)((bk >> tm.lo[1]) & ((1ull << tm.nb[1]) - 1ull));
+        const int c2 = (int)((bk >> tm.lo[2]) & ((1ull << tm.nb[2]) - 1ull));
+        if (rank == 3) {
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                "%3, %4}], [%5];" ::"r"(d),
+                "l"(mp), "r"(c0), "r"(c1), "r"(c2), "r"(mb)
+                : "memory");
+            continue;
+        }
+        const int c3 = (int)((bk >> tm.lo[3]) & ((1ull << tm.nb[3]) - 1ull));
+        if (rank == 4) {
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                "%3, %4, %5}], [%6];" ::"r"(d),
+                "l"(mp), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mb)
+                : "memory");
+            continue;
+        }
+        const int c4 = (int)((bk >> tm.lo[4]) & ((1ull << tm.nb[4]) - 1ull));
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4, %5, %6}], [%7];" ::"r"(d),
+            "l"(mp), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mb)
+            : "memory");
+    }
+}
 
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -206,14 +258,21 @@ template <int V> struct PairOcc { static constexpr int value = 3; };  // CTAs pe
 // most this many entries (the three CTAs of an SM still fit).
 constexpr int kPairTabSmem = 1024;
 
-template <int C, int V, int CL>
+// TM: the tile arrives as two tensor-map copies issued by thread 0 (one per
+// value of the pack bit, in the landing order of the layout the tile is
+// first read into; one launch = one task, the map of its state buffer in
+// ld) instead of per-thread 16-byte cp.async copies.  The buffer is placed
+// on a 1024-byte boundary (1 KB of slack in the dynamic shared memory).
+template <int C, int V, int CL, bool TM>
 __global__ void __launch_bounds__(128, PairOcc<V>::value)
     sweep_pair_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
-                      int64_t total, int* __restrict__ err, const __grid_constant__ PairQ pq) {
+                      int64_t total, int* __restrict__ err, const __grid_constant__ PairQ pq,
+                      const __grid_constant__ PairLoad ld) {
     using S = PairSweep<C>;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NB = S::NB;
     constexpr bool kPhase = V != V_LEAN, kZ = V == V_ZPHASE, kSTab = V == V_PHASE;
-    extern __shared__ __align__(128) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smdyn[];
+    unsigned char* smraw = TM ? smdyn + ((1024u - (smem_u32(smdyn) & 1023u)) & 1023u) : smdyn;
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     double* zacc = reinterpret_cast<double*>(smraw + S::SMEM_BYTES);  // kZ: [kZSlots][kZQ]
@@ -239,24 +298,52 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     // gt into buffer b, completing on that buffer's barrier (one arrival per
     // thread)
     auto issue = [&](int64_t gt, int b) {
+        if constexpr (TM) {
+            if (tid == 0) {
+                const SweepTask& T = tasks[0];
+                const TMap tm{T.c, T.g0, T.n1, T.g1, K};
+                fence_proxy_async();  // the buffer's generic accesses before the async writes
+                mbar_expect_tx(full + b, (uint32_t)S::BUF_BYTES);
+                tma_load_tile(smraw + b * S::BUF_BYTES, ld, tm.base(gt), full + b);
+            }
+            pend |= 1u << b;
+            return;
+        }
         const int ti = find_task(gt);
         const SweepTask& T = tasks[ti];
         const int64_t tile = gt - __ldg(prefix + ti);
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
         const float2* src = reinterpret_cast<const float2*>(T.psi) + tm.base(tile);
         float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
-        for (int q = tid; q < (1 << K) / 2; q += NT) {
-            const uint32_t e = (uint32_t)q * 2;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
-                         "l"(src + tm.gofs(e))
-                         : "memory");
+        // uniform choice of the copies' L2 fetch size
+        if (ld.l2 == 2) {
+            for (int q = tid; q < (1 << K) / 2; q += NT) {
+                const uint32_t e = (uint32_t)q * 2;
+                asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
+                             "l"(src + tm.gofs(e))
+                             : "memory");
+            }
+        } else if (ld.l2 == 1) {
+            for (int q = tid; q < (1 << K) / 2; q += NT) {
+                const uint32_t e = (uint32_t)q * 2;
+                asm volatile("cp.async.cg.shared.global.L2::128B [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
+                             "l"(src + tm.gofs(e))
+                             : "memory");
+            }
+        } else {
+            for (int q = tid; q < (1 << K) / 2; q += NT) {
+                const uint32_t e = (uint32_t)q * 2;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
+                             "l"(src + tm.gofs(e))
+                             : "memory");
+            }
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full + b)) : "memory");
         pend |= 1u << b;
     };
 
     if (tid == 0) {
-        for (int b = 0; b < NB; ++b) mbar_init(full + b, NT);
+        for (int b = 0; b < NB; ++b) mbar_init(full + b, TM ? 1 : NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (zon)
@@ -305,27 +392,31 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             if (nx < total && !failed) issue(nx, b);
         };
 
-        if (failed) {  // a copy timed out earlier: keep the cluster barriers in step
-            release();
-            continue;
-        }
         // the tile's cost table (warp 0), published by the barrier after the wait
         const TileTab& tt = ttab[tpar];
         if (kPhase && tid < 32) tile_tab_fill(&ttab[tpar], T.tprog, base, tid);
         tpar ^= 1u;
-        const int ok = mbar_wait_bounded(full + b, (phase >> b) & 1u) ? 1 : 0;
-        if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
+        // After a timed-out wait the CTA walks its remaining tiles without
+        // waiting, loading or storing (the copies stay pending on this phase
+        // until the exit drain): the barriers stay in step with the cluster
+        // and the loop keeps a single path.
+        const int ok = failed ? 0 : (mbar_wait_bounded(full + b, (phase >> b) & 1u) ? 1 : 0);
+        if (__syncthreads_and(ok)) {
+            phase ^= 1u << b;
+            pend &= ~(1u << b);
+        } else if (!failed) {
             if (tid == 0) atomicExch(err, 1);
             failed = true;
-            if (CL == 1) break;
-            release();
-            continue;
+            if (CL == 1) break;  // no cluster to keep in step
         }
-        phase ^= 1u << b;
-        pend &= ~(1u << b);
         int cur = nr & 1;
-        if (cur) S::template lds_dense<1>(buf, X, Y, tid);
-        else S::template lds_dense<0>(buf, X, Y, tid);
+        if constexpr (TM) {
+            if (cur) S::template lds_tma<1>(buf, X, Y, tid);
+            else S::template lds_tma<0>(buf, X, Y, tid);
+        } else {
+            if (cur) S::template lds_dense<1>(buf, X, Y, tid);
+            else S::template lds_dense<0>(buf, X, Y, tid);
+        }
         __syncthreads();  // dense reads done before the swizzled writes
         if (ntr == 0) release();
 
@@ -373,7 +464,7 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         }
         to_layout(0);
 
-        if (flags & T_STORE) {
+        if ((flags & T_STORE) && !failed) {
             float2* dst = reinterpret_cast<float2*>(T.psi) + base + tm.gofs(S::template e_thread<0>(tid));
             const uint64_t gP = tm.gofs(1u << P);
             if (T.c + T.n1 <= 8) {  // layout-0 registers (tile bits 8..12) in the second run: one shift
@@ -415,23 +506,27 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     }
 }
 
-template <int C, int V>
+template <int C, int V, bool TM = false>
 constexpr size_t pair_smem() {
     return PairSweep<C>::SMEM_BYTES + (V == V_ZPHASE ? PairSweep<C>::Z_BYTES : 0) +
-           (V == V_PHASE ? (size_t)kPairTabSmem * sizeof(float2) : 0);
+           (V == V_PHASE ? (size_t)kPairTabSmem * sizeof(float2) : 0) + (TM ? 1024 : 0);
 }
 
-template <int C, int V>
-static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
-    constexpr size_t smem = pair_smem<C, V>();
+template <int C, int V, bool TM>
+static cudaError_t launch_pair_tm(const SweepLaunch& L, int grid, cudaStream_t st) {
+    constexpr size_t smem = pair_smem<C, V, TM>();
     if (V != V_LEAN && !L.pq) return cudaErrorInvalidValue;  // the phase needs the Q tables
+    if (TM && (!L.load || !L.load->tma || L.ntasks != 1)) return cudaErrorInvalidValue;
     const PairQ pq = L.pq ? *L.pq : PairQ{};
+    PairLoad tm;
+    if (L.load) tm = *L.load;
+    else std::memset(&tm, 0, sizeof tm);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 1, TM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(sweep_pair_kernel<C, V, 4, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -449,13 +544,18 @@ static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t 
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, sweep_pair_kernel<C, V, 4>, L.tasks, L.tile_prefix, L.ntasks,
-                                           L.total_tiles, L.err, pq);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, sweep_pair_kernel<C, V, 4, TM>, L.tasks, L.tile_prefix, L.ntasks,
+                                           L.total_tiles, L.err, pq, tm);
         return note_launch(e);
     }
-    sweep_pair_kernel<C, V, 1><<<grid, PairSweep<C>::NT, smem, st>>>(L.tasks, L.tile_prefix, L.ntasks,
-                                                                      L.total_tiles, L.err, pq);
+    sweep_pair_kernel<C, V, 1, TM><<<grid, PairSweep<C>::NT, smem, st>>>(L.tasks, L.tile_prefix, L.ntasks,
+                                                                          L.total_tiles, L.err, pq, tm);
     return note_launch(cudaGetLastError());
+}
+
+template <int C, int V>
+static cudaError_t launch_pair_cfg(const SweepLaunch& L, int grid, cudaStream_t st) {
+    return L.load && L.load->tma ? launch_pair_tm<C, V, true>(L, grid, st) : launch_pair_tm<C, V, false>(L, grid, st);
 }
 
 cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st) {
@@ -472,7 +572,7 @@ cudaError_t launch_sweep_pair(const SweepLaunch& L, int grid, cudaStream_t st) {
 // (a multiple of four), else one CTA per resident slot.
 template <int V>
 static int pair_grid_v() {
-    auto kern = sweep_pair_kernel<2, V, 4>;
+    auto kern = sweep_pair_kernel<2, V, 4, false>;
     constexpr size_t smem = pair_smem<2, V>();
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
@@ -492,7 +592,7 @@ static int pair_grid_v() {
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V, 1>, PairSweep<2>::NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_pair_kernel<2, V, 1, false>, PairSweep<2>::NT, smem);
     if (per_sm < 1) per_sm = 1;
     return per_sm * sms;
 }

@@ -250,7 +250,7 @@ constexpr int kAdjTabSmem = 1024;
 template <int C>
 __global__ void __launch_bounds__(256, 1)
     sweep_pair_adj_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
-                          int64_t total, int* __restrict__ err, const __grid_constant__ PairAdjQ pq) {
+                          int64_t total, int* __restrict__ err, const __grid_constant__ PairAdjQ pq, int l2) {
     using S = PairAdj<C>;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NW = S::NW, NSLOT = S::NSLOT;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -286,11 +286,30 @@ __global__ void __launch_bounds__(256, 1)
         for (int a = 0; a < 2; ++a) {
             const float2* src = reinterpret_cast<const float2*>(a == 0 ? T.psi : T.lam) + base;
             float2* dst = buf + ((size_t)a << K);
-            for (int q = tid; q < (1 << K) / 2; q += NT) {
-                const uint32_t e = (uint32_t)q * 2;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + land<P>(e))),
-                             "l"(src + tm.gofs(e))
-                             : "memory");
+            // uniform choice of the copies' L2 fetch size (0 default, 1 128 B, 2 256 B)
+            if (l2 == 2) {
+                for (int q = tid; q < (1 << K) / 2; q += NT) {
+                    const uint32_t e = (uint32_t)q * 2;
+                    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(
+                                     smem_u32(dst + land<P>(e))),
+                                 "l"(src + tm.gofs(e))
+                                 : "memory");
+                }
+            } else if (l2 == 1) {
+                for (int q = tid; q < (1 << K) / 2; q += NT) {
+                    const uint32_t e = (uint32_t)q * 2;
+                    asm volatile("cp.async.cg.shared.global.L2::128B [%0], [%1], 16;" ::"r"(
+                                     smem_u32(dst + land<P>(e))),
+                                 "l"(src + tm.gofs(e))
+                                 : "memory");
+                }
+            } else {
+                for (int q = tid; q < (1 << K) / 2; q += NT) {
+                    const uint32_t e = (uint32_t)q * 2;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + land<P>(e))),
+                                 "l"(src + tm.gofs(e))
+                                 : "memory");
+                }
             }
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full)) : "memory");
@@ -443,7 +462,7 @@ static cudaError_t launch_pair_adj_cfg(const SweepLaunch& L, int grid, cudaStrea
     }
     if (!L.paq) return cudaErrorInvalidValue;  // the un-phase needs the Q tables
     sweep_pair_adj_kernel<C><<<grid, PairAdj<C>::NT, pair_adj_smem<C>(), st>>>(L.tasks, L.tile_prefix, L.ntasks,
-                                                                                L.total_tiles, L.err, *L.paq);
+                                                                                L.total_tiles, L.err, *L.paq, L.l2);
     return note_launch(cudaGetLastError());
 }
 

@@ -138,19 +138,7 @@ struct RunsSweep {
     __device__ static __forceinline__ void phase(float2 (&X)[NJ], float2 (&Y)[NJ], const SweepTask& T,
                                                  const TileTab& tt, uint32_t tid, const float2* __restrict__ tab,
                                                  int frame, const PairQ& pq) {
-        SlotCost<6> sc;
-        sc.template init_tile<Map<g>, 7>(tt, T.cprog[g], tid, frame, T.cost_lo);
-        const int top = T.tab_stride - 1;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int ia = SlotCost<6>::clamp_tab(sc.idx_noq(2 * j) + pq.q[g][2 * j], top);
-            const int ib = SlotCost<6>::clamp_tab(sc.idx_noq(2 * j + 1) + pq.q[g][2 * j + 1], top);
-            const float2 fa = tab[ia];
-            const float2 fb = tab[ib];
-            const float ar = X[j].x, br = X[j].y, ai = Y[j].x, bi = Y[j].y;
-            X[j] = make_float2(fmaf(ar, fa.x, -ai * fa.y), fmaf(br, fb.x, -bi * fb.y));
-            Y[j] = make_float2(fmaf(ar, fa.y, ai * fa.x), fmaf(br, fb.y, bi * fb.x));
-        }
+        pair_phase<Map<g>, 7>(X, Y, T.cprog[g], tt, tid, frame, T.cost_lo, tab, T.tab_stride - 1, pq.q[g]);
     }
 };
 

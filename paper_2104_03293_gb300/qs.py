@@ -21,6 +21,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_ENOTINT, QS_ESTATE = rang
 QS_C64, QS_C128 = 0, 1
 QS_OBJ_ENERGY, QS_OBJ_GROUND = 0, 1
 QS_PATH_TILED, QS_PATH_PLAIN = 0, 1
+PLAN_RULE_INTS = 7  # QS_PLAN_RULE_INTS
 MIN_PHYS_QUBITS = 13
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_ENOTINT",
@@ -78,6 +79,7 @@ _SIGS = {
     "qs_aqa_chain_2nd": [_I, _D, _PD, _PD, _PD, _PD, _PD],
     "qs_launch_count": [_PI64],
     "qs_plan_shape": [_I, _I, _I, _PI, _PI, _PI, _PI, _PI, _PI],
+    "qs_pair_tile_map": [_I, _I, _I, _I, _I, _I, _PI, _PI, _PI, _PI, _PI, _PI],
     "qs_last_error": [],
     "qs_version": [],
     "qs_batch_create": [ctypes.POINTER(_P), _I, _PI, _I, _P],
@@ -279,13 +281,20 @@ class State:
         return r.value, sp.value, ms.value
 
     def plan_rule(self) -> tuple:
-        """(runs_a, split, cmin, ctas_per_sm, pair_cluster) of the handle."""
-        v = (ctypes.c_int * 5)()
+        """(runs_a, split, cmin, ctas_per_sm, pair_cluster, pair_tma, pair_l2)
+        of the handle."""
+        v = (ctypes.c_int * PLAN_RULE_INTS)()
         _check(lib().qs_get_plan_rule(self._h, v))
         return tuple(v)
 
     def set_plan_rule(self, rule):
-        v = (ctypes.c_int * 5)(*[int(x) for x in rule])
+        """Set a plan rule; a shorter rule keeps the remaining fields at their
+        defaults (cp.async tile loads, default L2 fetch size)."""
+        r = [int(x) for x in rule]
+        if len(r) > PLAN_RULE_INTS or len(r) < 5:
+            raise ValueError(f"a plan rule has 5 to {PLAN_RULE_INTS} ints")
+        r += [0] * (PLAN_RULE_INTS - len(r))
+        v = (ctypes.c_int * PLAN_RULE_INTS)(*r)
         _check(lib().qs_set_plan_rule(self._h, v))
 
     def autotune_plan(self, p_trial: int = 2, cache: Optional[str] = None):
@@ -300,14 +309,14 @@ class State:
             import json
             with open(cache) as f:
                 entry = json.load(f).get(key)
-            if entry:
+            if entry and len(entry["rule"]) == PLAN_RULE_INTS:
                 self.set_plan_rule(entry["rule"])
                 return tuple(entry["rule"]), float(entry["ms"]), [(tuple(r), m) for r, m in entry["candidates"]]
-        cap = 64
-        rules, ms_c = (ctypes.c_int * (5 * cap))(), (ctypes.c_double * cap)()
-        best, nc, ms = (ctypes.c_int * 5)(), ctypes.c_int(), ctypes.c_double()
+        cap, k = 64, PLAN_RULE_INTS
+        rules, ms_c = (ctypes.c_int * (k * cap))(), (ctypes.c_double * cap)()
+        best, nc, ms = (ctypes.c_int * k)(), ctypes.c_int(), ctypes.c_double()
         _check(lib().qs_autotune_ex(self._h, int(p_trial), cap, ctypes.byref(nc), rules, ms_c, best, ctypes.byref(ms)))
-        cands = [(tuple(rules[5 * i:5 * i + 5]), ms_c[i]) for i in range(min(nc.value, cap))]
+        cands = [(tuple(rules[k * i:k * i + k]), ms_c[i]) for i in range(min(nc.value, cap))]
         if cache:
             import json
             data = {}
@@ -384,6 +393,22 @@ def plan_shapes(n: int, dtype: int = QS_C64):
             break
         out.append(dict(zip(("kind", "K", "c", "g0", "n1", "g1"), (v.value for v in vals))))
     return out
+
+
+def pair_tile_map(n: int, c: int, g0: int, n1: int, g1: int, g: int):
+    """Tensor-map view of a strided complex64 tile shape for a first read into
+    layout g (host only): dict(rank, kbit, start, width, box, landing), or
+    None when the shape does not fit a five-dimensional box."""
+    rank, kbit = ctypes.c_int(), ctypes.c_int()
+    arr = [(ctypes.c_int * 5)() for _ in range(3)]
+    land = (ctypes.c_int * 13)()
+    rc = lib().qs_pair_tile_map(int(n), int(c), int(g0), int(n1), int(g1), int(g), ctypes.byref(rank),
+                                ctypes.byref(kbit), arr[0], arr[1], arr[2], land)
+    if rc != QS_OK:
+        return None
+    r = rank.value
+    return {"rank": r, "kbit": kbit.value, "start": list(arr[0])[:r], "width": list(arr[1])[:r],
+            "box": list(arr[2])[:r], "landing": list(land)}
 
 
 def aqa_angles(tau: float, s) -> tuple:
