@@ -367,6 +367,8 @@ def main():
     ap.add_argument("--ref-n", type=int, default=26)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the batched / n=26 gradient / Adam figures")
+    ap.add_argument("--plan-rule", default=None,
+                    help="comma-separated plan rule for both states, applied without the autotuner")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,9 +404,16 @@ def main():
     # QS_TUNE_CACHE makes later runs skip the search)
     tune_cache = os.environ.get("QS_TUNE_CACHE")
     st.set_ising(inst.h, inst.edges, inst.J)
-    rule, rule_ms, cands = st.autotune_plan(2, cache=tune_cache)
     st2.set_ising(inst2.h, inst2.edges, inst2.J)
-    rule2, rule2_ms, cands2 = st2.autotune_plan(2, cache=tune_cache)
+    if args.plan_rule:
+        fixed = [int(x) for x in args.plan_rule.split(",")]
+        st.set_plan_rule(fixed)
+        st2.set_plan_rule(fixed)
+        rule, rule_ms, cands = st.plan_rule(), None, []
+        rule2, rule2_ms, cands2 = st2.plan_rule(), None, []
+    else:
+        rule, rule_ms, cands = st.autotune_plan(2, cache=tune_cache)
+        rule2, rule2_ms, cands2 = st2.autotune_plan(2, cache=tune_cache)
     _, sweeps = st.plan_info(p)
     _, sweeps2 = st2.plan_info(p)
     stream = torch.cuda.current_stream()

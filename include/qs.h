@@ -227,11 +227,14 @@ int qs_set_shape_rule(qs_handle h, int runs_a, int split);
  *                    shape does not fit a five-dimensional box);
  *   [6] pair_l2      L2 fetch size of the strided packed-pair tile loads
  *                    (forward and reverse sweeps): 0 the default, 1 128
- *                    bytes, 2 256 bytes.
+ *                    bytes, 2 256 bytes;
+ *   [7] order        1: the strided shapes in reverse order, so that the
+ *                    zig-zag schedule merges the sweeps of another shape
+ *                    around the phases (0: the planned order).
  * Every rule gives the same results up to rounding order (the load fields
  * give bit-identical states).  qs_set_plan_rule re-plans the current Ising
  * cost when the shape fields change.  Errors: QS_EINVAL. */
-#define QS_PLAN_RULE_INTS 7
+#define QS_PLAN_RULE_INTS 8
 int qs_set_plan_rule(qs_handle h, const int* rule);
 int qs_get_plan_rule(qs_handle h, int* rule);
 
@@ -240,8 +243,9 @@ int qs_get_plan_rule(qs_handle h, int* rule);
  * fastest.  Search, coordinate by coordinate: tile shapes first (contiguous
  * shape A; for complex64 states of 24 qubits and more the run-structured A
  * with split bits 20, 22 and 24; each with cmin 2 and 3), then, for the best
- * shapes, one CTA per SM fewer than fit and (complex64) the strided sweeps
- * without clusters, then (complex64) the strided tile loads: cp.async with
+ * shapes, the strided shapes in reverse order, one CTA per SM fewer than
+ * fit and (complex64) the strided sweeps without clusters, then
+ * (complex64) the strided tile loads: cp.async with
  * 128- or 256-byte L2 fetches, tensor-map copies with the default or 256-
  * byte fetches.  Reports the measured candidates (up to max_cand rules of
  * QS_PLAN_RULE_INTS ints in cand_rules with their times in cand_ms, the

@@ -422,7 +422,7 @@ int qs_set_shape_rule(qs_handle h, int runs_a, int split) {
     if (int rc = check_handle(h)) return rc;
     if (runs_a < -1 || runs_a > 1 || split < -1 || split >= h->nphys + 1)
         return set_error(QS_EINVAL, "qs_set_shape_rule: runs_a in {-1, 0, 1}, split in [-1, n]");
-    h->rule = ShapeRule{runs_a, split, h->rule.cmin};
+    h->rule = ShapeRule{runs_a, split, h->rule.cmin, h->rule.order};
     return replan(h);
 }
 
@@ -430,14 +430,16 @@ int qs_set_plan_rule(qs_handle h, const int* rule) {
     if (int rc = check_handle(h)) return rc;
     if (!rule) return set_error(QS_EINVAL, "qs_set_plan_rule: rule is NULL");
     const int runs_a = rule[0], split = rule[1], cmin = rule[2], cps = rule[3], cl = rule[4], tma = rule[5],
-              l2 = rule[6];
+              l2 = rule[6], order = rule[7];
     if (runs_a < -1 || runs_a > 1 || split < -1 || split >= h->nphys + 1 || !(cmin == -1 || cmin == 2 || cmin == 3) ||
-        cps < 0 || cps > 32 || !(cl == 1 || cl == 4) || tma < 0 || tma > 1 || l2 < 0 || l2 > 2)
+        cps < 0 || cps > 32 || !(cl == 1 || cl == 4) || tma < 0 || tma > 1 || l2 < 0 || l2 > 2 || order < 0 ||
+        order > 1)
         return set_error(QS_EINVAL, "qs_set_plan_rule: runs_a in {-1, 0, 1}, split in [-1, n], cmin in {-1, 2, 3}, "
                                     "ctas_per_sm in [0, 32], pair_cluster in {1, 4}, pair_tma in {0, 1}, pair_l2 in "
-                                    "{0, 1, 2}");
-    const bool reshape = runs_a != h->rule.runs_a || split != h->rule.split || cmin != h->rule.cmin;
-    h->rule = ShapeRule{runs_a, split, cmin};
+                                    "{0, 1, 2}, order in {0, 1}");
+    const ShapeRule nr{runs_a, split, cmin, order};
+    const bool reshape = !same_shapes(nr, h->rule);
+    h->rule = nr;
     h->ctas_per_sm = cps;
     h->pair_cluster = cl;
     h->pair_tma = tma;
@@ -455,6 +457,7 @@ int qs_get_plan_rule(qs_handle h, int* rule) {
     rule[4] = h->pair_cluster;
     rule[5] = h->pair_tma;
     rule[6] = h->pair_l2;
+    rule[7] = h->rule.order;
     return QS_OK;
 }
 
@@ -507,7 +510,7 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
     double best = 1e300;
     Cand pick{ShapeRule{0, page_bit_for(h->dtype), -1}, 0, 4, 0, 0, 1e300};
     auto measure = [&](Cand c) {
-        const bool reshape = c.r.runs_a != h->rule.runs_a || c.r.split != h->rule.split || c.r.cmin != h->rule.cmin;
+        const bool reshape = !same_shapes(c.r, h->rule);
         apply(c);
         c.ms = 1e300;
         if (reshape && (rc = replan(h))) return;
@@ -529,6 +532,13 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
     for (const ShapeRule& r : shapes) {
         measure(Cand{r, 0, 4, 0, 0, 0.0});
         if (rc) break;
+    }
+    // the best shapes with the strided shapes in reverse order (another
+    // shape's sweeps merged around the phases)
+    if (!rc && pick.r.order == 0) {
+        ShapeRule r = pick.r;
+        r.order = 1;
+        measure(Cand{r, 0, 4, 0, 0, 0.0});
     }
     // stage 2, launch: one CTA per SM fewer than fit, and (complex64) the
     // strided packed-pair sweeps without their 4-CTA clusters
@@ -564,12 +574,13 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
     if (ncand) *ncand = (int)done.size();
     for (int i = 0; i < (int)done.size() && i < max_cand; ++i) {
         const Cand& c = done[i];
-        const int v[kPlanRuleInts] = {c.r.runs_a, c.r.split, c.r.cmin, c.cps, c.cl, c.tma, c.l2};
+        const int v[kPlanRuleInts] = {c.r.runs_a, c.r.split, c.r.cmin, c.cps, c.cl, c.tma, c.l2, c.r.order};
         for (int k = 0; k < kPlanRuleInts; ++k) cand_rules[kPlanRuleInts * i + k] = v[k];
         cand_ms[i] = c.ms;
     }
     if (best_rule) {
-        const int v[kPlanRuleInts] = {pick.r.runs_a, pick.r.split, pick.r.cmin, pick.cps, pick.cl, pick.tma, pick.l2};
+        const int v[kPlanRuleInts] = {pick.r.runs_a, pick.r.split, pick.r.cmin, pick.cps,
+                                      pick.cl,         pick.tma,    pick.l2,     pick.r.order};
         for (int k = 0; k < kPlanRuleInts; ++k) best_rule[k] = v[k];
     }
     if (best_ms) *best_ms = best;

@@ -27,7 +27,7 @@ constexpr int kMaxRounds = 8;        // rounds (layers) fused into one sweep
 constexpr int kMaxShapes = 4;        // tile shapes per plan
 constexpr int kMaxLayouts = 3;       // register layouts per tile shape
 constexpr int kRunBits = 8;          // run-structured shape A: runs of 2^8 amplitudes
-constexpr int kPlanRuleInts = 7;     // ints of a plan rule (QS_PLAN_RULE_INTS)
+constexpr int kPlanRuleInts = 8;     // ints of a plan rule (QS_PLAN_RULE_INTS)
 #define QS_MAX_LAYERS_PREP 1024          // layers per preparation call
 
 // Register-layout parameters per kernel configuration.

@@ -207,6 +207,7 @@ std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, Sh
     // shapes whose low run ends where their high run starts are one run
     for (auto& s : v)
         if (s.kind == 1 && s.g0 + s.n1 == s.g1) { s.n1 = 0; s.g1 = s.g0; }
+    if (rule.order == 1 && v.size() > 2) std::reverse(v.begin() + 1, v.end());
     return v;
 }
 

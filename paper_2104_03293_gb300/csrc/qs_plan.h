@@ -62,12 +62,17 @@ inline int page_bit_for(int dtype) { return dtype == 0 ? 18 : 17; }
 // rule (run-structured from 33 qubits); split = index bit from which the
 // strided shapes' qubits are dealt out evenly, -1 = default (bit 22 with a
 // run-structured A, else the 2 MB page bit); cmin = carried bits of the
-// strided shapes (each holds 13 - cmin targets in rows of 2^cmin amplitudes).
+// strided shapes (each holds 13 - cmin targets in rows of 2^cmin amplitudes);
+// order = 1 reverses the strided shapes (which of them the zig-zag merges).
 struct ShapeRule {
     int runs_a = -1;
     int split = -1;
     int cmin = -1;  // carried low bits of the strided shapes (2 or 3; -1 = the kernel default, 2)
+    int order = 0;  // 1: the strided shapes in reverse order (the zig-zag merges the last shape's sweeps)
 };
+inline bool same_shapes(const ShapeRule& a, const ShapeRule& b) {
+    return a.runs_a == b.runs_a && a.split == b.split && a.cmin == b.cmin && a.order == b.order;
+}
 std::vector<Shape> make_shapes(int nphys, const KernelCfg& cfg, int page_bit, ShapeRule rule = ShapeRule{});
 
 // Tensor-map view of a strided packed-pair tile (complex64, K = 13, c = 2 or

@@ -21,7 +21,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_ENOTINT, QS_ESTATE = rang
 QS_C64, QS_C128 = 0, 1
 QS_OBJ_ENERGY, QS_OBJ_GROUND = 0, 1
 QS_PATH_TILED, QS_PATH_PLAIN = 0, 1
-PLAN_RULE_INTS = 7  # QS_PLAN_RULE_INTS
+PLAN_RULE_INTS = 8  # QS_PLAN_RULE_INTS
 MIN_PHYS_QUBITS = 13
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_ENOTINT",
@@ -281,15 +281,16 @@ class State:
         return r.value, sp.value, ms.value
 
     def plan_rule(self) -> tuple:
-        """(runs_a, split, cmin, ctas_per_sm, pair_cluster, pair_tma, pair_l2)
-        of the handle."""
+        """(runs_a, split, cmin, ctas_per_sm, pair_cluster, pair_tma, pair_l2,
+        order) of the handle."""
         v = (ctypes.c_int * PLAN_RULE_INTS)()
         _check(lib().qs_get_plan_rule(self._h, v))
         return tuple(v)
 
     def set_plan_rule(self, rule):
         """Set a plan rule; a shorter rule keeps the remaining fields at their
-        defaults (cp.async tile loads, default L2 fetch size)."""
+        defaults (cp.async tile loads, default L2 fetch size, planned order
+        of the strided shapes)."""
         r = [int(x) for x in rule]
         if len(r) > PLAN_RULE_INTS or len(r) < 5:
             raise ValueError(f"a plan rule has 5 to {PLAN_RULE_INTS} ints")

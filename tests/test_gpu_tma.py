@@ -3,7 +3,8 @@ fields pair_tma and pair_l2): tensor-map copies, and cp.async copies with
 128- or 256-byte L2 fetches, give states bit-identical to the default
 cp.async loads (the same arithmetic on the same values), and the oracle's
 state where the oracle runs: the whole state at n = 24 and 27 (lean
-strided sweeps), a product instance of two oracle-sized components at
+strided sweeps) and n = 26 with the strided shapes in reverse order (the
+packed-pair shape's sweeps merged around the phases), a product instance of two oracle-sized components at
 n = 32 (two strided shapes of 2^3-amplitude rows, the merged sweeps
 included) and n = 34 (the bench's shapes and the default ones).
 """
@@ -27,13 +28,13 @@ def qs():
 
 
 def _set_load(st, rule, tma, l2):
-    r = list(rule) + [0] * (7 - len(rule))
+    r = list(rule) + [0] * (8 - len(rule))
     r[5], r[6] = tma, l2
     st.set_plan_rule(r)
 
 
-@pytest.mark.parametrize("n", [24, 27])
-def test_loads_against_oracle(qs, n):
+@pytest.mark.parametrize("n,order", [(24, 0), (27, 0), (26, 1)])
+def test_loads_against_oracle(qs, n, order):
     inst = I.erdos_renyi_ising(n, I.workload_seed(7, n))
     s = np.arange(1, 6) / 6.0
     g, b = oracle.aqa_angles(0.8, s)
@@ -41,7 +42,9 @@ def test_loads_against_oracle(qs, n):
     st = qs.State(n)
     try:
         st.set_instance(inst)
-        rule = st.plan_rule()
+        rule = list(st.plan_rule())
+        rule[7] = order  # 1: the packed-pair shape last, its sweeps merged
+        st.set_plan_rule(rule)
         st.evolve(g, b)
         base = st.copy_state()
         assert np.linalg.norm(base.astype(np.complex128) - ref) <= 1e-4
