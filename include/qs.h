@@ -225,9 +225,8 @@ int qs_set_shape_rule(qs_handle h, int runs_a, int split);
  *                    thread; 0: with per-thread 16-byte cp.async copies
  *                    (the tensor-map copies fall back to these where a
  *                    shape does not fit a five-dimensional box);
- *   [6] pair_l2      L2 fetch size of the strided packed-pair tile loads
- *                    (forward and reverse sweeps): 0 the default, 1 128
- *                    bytes, 2 256 bytes;
+ *   [6] pair_l2      L2 promotion of the tensor-map tile copies: 0 none,
+ *                    1 128 bytes, 2 256 bytes;
  *   [7] order        1: the strided shapes in reverse order, so that the
  *                    zig-zag schedule merges the sweeps of another shape
  *                    around the phases (0: the planned order).
@@ -245,9 +244,8 @@ int qs_get_plan_rule(qs_handle h, int* rule);
  * with split bits 20, 22 and 24; each with cmin 2 and 3), then, for the best
  * shapes, the strided shapes in reverse order, one CTA per SM fewer than
  * fit and (complex64) the strided sweeps without clusters, then
- * (complex64) the strided tile loads: cp.async with
- * 128- or 256-byte L2 fetches, tensor-map copies with the default or 256-
- * byte fetches.  Reports the measured candidates (up to max_cand rules of
+ * (complex64) tensor-map tile copies with no or 256-byte L2 promotion.
+ * Reports the measured candidates (up to max_cand rules of
  * QS_PLAN_RULE_INTS ints in cand_rules with their times in cand_ms, the
  * count in ncand) and the kept rule (best_rule, QS_PLAN_RULE_INTS ints) with
  * its time; any output may be NULL when max_cand = 0.  Overwrites the

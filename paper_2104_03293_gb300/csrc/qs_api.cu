@@ -233,7 +233,7 @@ struct qs_state {
     int ctas_per_sm = 0;                 // launch rule: persistent CTAs per SM (0 = as many as fit)
     int pair_cluster = 4;                // launch rule: strided packed-pair sweeps in 4-CTA clusters or not
     int pair_tma = 0;                    // launch rule: strided packed-pair forward tiles by tensor-map copies
-    int pair_l2 = 0;                     // launch rule: L2 fetch size of those tile loads (0 default, 1 128 B, 2 256 B)
+    int pair_l2 = 0;                     // launch rule: L2 promotion of the tensor-map tile copies (0 none, 1 128 B, 2 256 B)
     int sms = 0;                         // multiprocessors of the device
     std::vector<double> ising_h, ising_J;  // the last qs_set_ising input, to re-plan
     std::vector<int32_t> ising_e;
@@ -372,9 +372,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tile loads of a strided packed-pair forward sweep over psi whose tiles are
-// first read into layout g: tensor-map copies when the rule asks for them
-// and the shape fits (pair_tma_dims), else cp.async; the L2 fetch size in
-// both cases.
+// first read into layout g: tensor-map copies (with the rule's L2
+// promotion) when the rule asks for them and the shape fits
+// (pair_tma_dims), else cp.async.
 static PairLoad make_pair_load(qs_handle h, const Shape& s, void* psi, int g) {
     PairLoad L;
     std::memset(&L, 0, sizeof L);
@@ -556,11 +556,11 @@ int qs_autotune_ex(qs_handle h, int p_trial, int max_cand, int* ncand, int* cand
             if (rc) break;
         }
     }
-    // stage 3 (complex64), the strided packed-pair tile loads: the copies'
-    // L2 fetch size (128 or 256 bytes), and tensor-map copies
+    // stage 3 (complex64), the strided packed-pair tile loads: tensor-map
+    // copies with the default or 256-byte L2 promotion
     if (!rc && h->dtype == QS_C64) {
         const Cand base = pick;
-        const int loads[4][2] = {{0, 1}, {0, 2}, {1, 0}, {1, 2}};
+        const int loads[2][2] = {{1, 0}, {1, 2}};
         for (const auto& ld : loads) {
             measure(Cand{base.r, base.cps, base.cl, ld[0], ld[1], 0.0});
             if (rc) break;
@@ -830,7 +830,6 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
                       reinterpret_cast<const int64_t*>(dblob + rev_pre[i]), derr};
         L.pairc = pair_choice(h->dtype, 1, sh.kind, sh.c, 0);
         L.paq = &I.pair_adj_q[rev[i].shape];
-        L.l2 = h->pair_l2;
         e = launch_sweep(L, grid_for(h, L.pairc ? 3 : L.kind, 1), h->st);
         if (e != cudaSuccess) return cuda_error(e, "adjoint sweep launch");
         if (red_cnt[i]) {

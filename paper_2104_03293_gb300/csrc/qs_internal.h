@@ -126,14 +126,13 @@ struct PairAdjQ {
 };
 
 // How a packed-pair forward launch loads its strided tiles.  tma = 0:
-// per-thread 16-byte cp.async copies, with the L2 fetch size l2 (0: default,
-// 1: 128 bytes, 2: 256 bytes; the prefetch-size hint of the copies).
-// tma = 1: two tensor-map copies per tile (one launch = one task), the map
-// of its state buffer (rank 3 to 5, float elements, no swizzle, dimensions
-// in the landing order of pair_tma_pos; its L2 promotion set from l2) and,
-// per dimension, the first global index bit and the bits it spans, from
-// which the kernel forms a tile's coordinates; the pack bit (global bit
-// kbit) selects one of the tile's two box copies.
+// per-thread 16-byte cp.async copies.  tma = 1: two tensor-map copies per
+// tile (one launch = one task), the map of its state buffer (rank 3 to 5,
+// float elements, no swizzle, dimensions in the landing order of
+// pair_tma_pos; L2 promotion l2: 0 none, 1 128 bytes, 2 256 bytes) and, per
+// dimension, the first global index bit and the bits it spans, from which
+// the kernel forms a tile's coordinates; the pack bit (global bit kbit)
+// selects one of the tile's two box copies.
 struct PairLoad {
     CUtensorMap map;
     int lo[5], nb[5];
@@ -158,7 +157,6 @@ struct SweepLaunch {
     const PairAdjQ* paq = nullptr; // host: Q tables of the shape (packed-pair adjoint sweeps)
     int cluster = 4;               // strided packed-pair forward: 4-CTA clusters (line sharing) or 1
     const PairLoad* load = nullptr;  // host: strided packed-pair forward tile loads (null: cp.async, default L2)
-    int l2 = 0;                    // packed-pair adjoint: L2 fetch size of the tile copies (as PairLoad::l2)
 };
 
 // Cost program: the Ising cost of Eq. (HC) specialised to one register layout.

@@ -55,7 +55,8 @@ struct PairSweep {
     static constexpr int NB = 1;  // tile buffers per CTA
     static constexpr size_t BUF_BYTES = (size_t)8 << K;
     static constexpr size_t TT_OFF = NB * BUF_BYTES + 64;  // two TileTabs (by tile parity)
-    static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    static constexpr size_t KOFF_OFF = TT_OFF + 2 * sizeof(TileTab);  // 32 tile-copy offsets (uint64)
+    static constexpr size_t SMEM_BYTES = KOFF_OFF + 32 * sizeof(uint64_t);
     // V_ZPHASE: FP64 spin-expectation accumulators [kZSlots][kZQ], then the warp sums
     static constexpr size_t Z_BYTES = (size_t)kZSlots * kZQ * 8 + (size_t)(NT / 32) * (K + 1) * 4;
     static_assert(SMEM_BYTES % 8 == 0, "accumulators follow the tile tables");
@@ -252,7 +253,12 @@ __device__ __forceinline__ void cluster_sync_all() {
 // share are fetched once.  Every CTA of a cluster walks the same number of
 // tiles (the tile count and the grid are multiples of four) and passes the
 // barrier once per tile, also after a timed-out wait.
-template <int V> struct PairOcc { static constexpr int value = 3; };  // CTAs per SM (every variant)
+// CTAs per SM: three (168 registers a thread); QS_PHASE_OCC sets it for the
+// sweeps that apply a phase (2: 255 registers, no spills, 8 warps per SM).
+#ifndef QS_PHASE_OCC
+#define QS_PHASE_OCC 3
+#endif
+template <int V> struct PairOcc { static constexpr int value = (V == V_PHASE || V == V_ZPHASE) ? QS_PHASE_OCC : 3; };
 
 // V_PHASE stages the layer table of its phase in shared memory when it has at
 // most this many entries (the three CTAs of an SM still fit).
@@ -275,6 +281,7 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     unsigned char* smraw = TM ? smdyn + ((1024u - (smem_u32(smdyn) & 1023u)) & 1023u) : smdyn;
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
+    uint64_t* koff = reinterpret_cast<uint64_t*>(smraw + S::KOFF_OFF);
     double* zacc = reinterpret_cast<double*>(smraw + S::SMEM_BYTES);  // kZ: [kZSlots][kZQ]
     float* zred = reinterpret_cast<float*>(smraw + S::SMEM_BYTES + (size_t)kZSlots * kZQ * 8);
     float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // kSTab: [kPairTabSmem]
@@ -313,31 +320,17 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         const SweepTask& T = tasks[ti];
         const int64_t tile = gt - __ldg(prefix + ti);
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-        const float2* src = reinterpret_cast<const float2*>(T.psi) + tm.base(tile);
-        float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
-        // uniform choice of the copies' L2 fetch size
-        if (ld.l2 == 2) {
-            for (int q = tid; q < (1 << K) / 2; q += NT) {
-                const uint32_t e = (uint32_t)q * 2;
-                asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
-                             "l"(src + tm.gofs(e))
-                             : "memory");
-            }
-        } else if (ld.l2 == 1) {
-            for (int q = tid; q < (1 << K) / 2; q += NT) {
-                const uint32_t e = (uint32_t)q * 2;
-                asm volatile("cp.async.cg.shared.global.L2::128B [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
-                             "l"(src + tm.gofs(e))
-                             : "memory");
-            }
-        } else {
-            for (int q = tid; q < (1 << K) / 2; q += NT) {
-                const uint32_t e = (uint32_t)q * 2;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + land<P>(e))),
-                             "l"(src + tm.gofs(e))
-                             : "memory");
-            }
-        }
+        // thread t copies elements e = 2t + 256k, k < 32: the landing map and
+        // the global offset split into a per-thread part and the k part
+        // (koff[k] = gofs(256 k), the same for every tile of the launch)
+        const uint32_t e_t = 2u * tid;
+        const float2* src = reinterpret_cast<const float2*>(T.psi) + tm.base(tile) + tm.gofs(e_t);
+        const uint32_t sb = smem_u32(smraw + b * S::BUF_BYTES), lt = land<P>(e_t);
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + 8u * (lt ^ land<P>(256u * k))),
+                         "l"(src + koff[k])
+                         : "memory");
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full + b)) : "memory");
         pend |= 1u << b;
     };
@@ -345,6 +338,10 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     if (tid == 0) {
         for (int b = 0; b < NB; ++b) mbar_init(full + b, TM ? 1 : NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (!TM && tid < 32) {  // the launch's tiles share one shape
+        const SweepTask& T0 = tasks[0];
+        koff[tid] = TMap{T0.c, T0.g0, T0.n1, T0.g1, K}.gofs(256u * tid);
     }
     if (zon)
         for (int i = (int)tid; i < kZSlots * kZQ; i += NT) zacc[i] = 0.0;

@@ -56,7 +56,8 @@ struct PairAdj {
                          NSLOT = 2 * kMaxRounds;
     static constexpr size_t TILE_BYTES = (size_t)8 << K;
     static constexpr size_t TT_OFF = 3 * TILE_BYTES + 64 + (size_t)NW * NSLOT * 8;  // two TileTabs
-    static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    static constexpr size_t KOFF_OFF = TT_OFF + 2 * sizeof(TileTab);  // 16 tile-copy offsets (uint64)
+    static constexpr size_t SMEM_BYTES = KOFF_OFF + 16 * sizeof(uint64_t);
     // compile-time tile bits of layout g: slot bit 0 is the pack bit
     template <int g> struct Map {
         __host__ __device__ static constexpr int slot(int b) {
@@ -250,7 +251,7 @@ constexpr int kAdjTabSmem = 1024;
 template <int C>
 __global__ void __launch_bounds__(256, 1)
     sweep_pair_adj_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
-                          int64_t total, int* __restrict__ err, const __grid_constant__ PairAdjQ pq, int l2) {
+                          int64_t total, int* __restrict__ err, const __grid_constant__ PairAdjQ pq) {
     using S = PairAdj<C>;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ, P = S::P, NW = S::NW, NSLOT = S::NSLOT;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(256, 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + 3 * S::TILE_BYTES);
     double* red = reinterpret_cast<double*>(smraw + 3 * S::TILE_BYTES + 64);
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
+    uint64_t* koff = reinterpret_cast<uint64_t*>(smraw + S::KOFF_OFF);
     float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // [kAdjTabSmem]
     const uint32_t tid = threadIdx.x;
     uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
@@ -281,36 +283,21 @@ __global__ void __launch_bounds__(256, 1)
         const SweepTask& T = tasks[ti];
         const int64_t tile = gt - __ldg(prefix + ti);
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-        const uint64_t base = tm.base(tile);
+        // thread t copies elements e = 2t + 512k, k < 16, of each array: the
+        // landing map and the global offset split into a per-thread part and
+        // the k part (koff[k] = gofs(512 k), the same for every tile)
+        const uint32_t e_t = 2u * tid;
+        const uint64_t off_t = tm.base(tile) + tm.gofs(e_t);
+        const uint32_t lt = land<P>(e_t);
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            const float2* src = reinterpret_cast<const float2*>(a == 0 ? T.psi : T.lam) + base;
-            float2* dst = buf + ((size_t)a << K);
-            // uniform choice of the copies' L2 fetch size (0 default, 1 128 B, 2 256 B)
-            if (l2 == 2) {
-                for (int q = tid; q < (1 << K) / 2; q += NT) {
-                    const uint32_t e = (uint32_t)q * 2;
-                    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(
-                                     smem_u32(dst + land<P>(e))),
-                                 "l"(src + tm.gofs(e))
-                                 : "memory");
-                }
-            } else if (l2 == 1) {
-                for (int q = tid; q < (1 << K) / 2; q += NT) {
-                    const uint32_t e = (uint32_t)q * 2;
-                    asm volatile("cp.async.cg.shared.global.L2::128B [%0], [%1], 16;" ::"r"(
-                                     smem_u32(dst + land<P>(e))),
-                                 "l"(src + tm.gofs(e))
-                                 : "memory");
-                }
-            } else {
-                for (int q = tid; q < (1 << K) / 2; q += NT) {
-                    const uint32_t e = (uint32_t)q * 2;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + land<P>(e))),
-                                 "l"(src + tm.gofs(e))
-                                 : "memory");
-                }
-            }
+            const float2* src = reinterpret_cast<const float2*>(a == 0 ? T.psi : T.lam) + off_t;
+            const uint32_t sb = smem_u32(buf + ((size_t)a << K));
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + 8u * (lt ^ land<P>(512u * k))),
+                             "l"(src + koff[k])
+                             : "memory");
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(full)) : "memory");
         pending = true;
@@ -319,6 +306,10 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0) {
         mbar_init(full, NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 16) {  // the launch's tiles share one shape
+        const SweepTask& T0 = tasks[0];
+        koff[tid] = TMap{T0.c, T0.g0, T0.n1, T0.g1, K}.gofs(512u * tid);
     }
     // the table of the (first) layer whose phase this sweep un-applies
     int slayer = -1;
@@ -462,7 +453,7 @@ static cudaError_t launch_pair_adj_cfg(const SweepLaunch& L, int grid, cudaStrea
     }
     if (!L.paq) return cudaErrorInvalidValue;  // the un-phase needs the Q tables
     sweep_pair_adj_kernel<C><<<grid, PairAdj<C>::NT, pair_adj_smem<C>(), st>>>(L.tasks, L.tile_prefix, L.ntasks,
-                                                                                L.total_tiles, L.err, *L.paq, L.l2);
+                                                                                L.total_tiles, L.err, *L.paq);
     return note_launch(cudaGetLastError());
 }
 

@@ -146,8 +146,11 @@ constexpr int kRunsTabSmem = 1024;  // V_PHASE: staged layer table entries
 
 }  // namespace
 
+#ifndef QS_PHASE_OCC
+#define QS_PHASE_OCC 3
+#endif
 template <int V>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
     sweep_runs_kernel(const SweepTask* __restrict__ tasks, const int64_t* __restrict__ prefix, int ntasks,
                       int64_t total, int* __restrict__ err, const __grid_constant__ PairQ pq) {
     using S = RunsSweep;
