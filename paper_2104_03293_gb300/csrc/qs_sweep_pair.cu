@@ -56,7 +56,10 @@ struct PairSweep {
     static constexpr size_t BUF_BYTES = (size_t)8 << K;
     static constexpr size_t TT_OFF = NB * BUF_BYTES + 64;  // two TileTabs (by tile parity)
     static constexpr size_t KOFF_OFF = TT_OFF + 2 * sizeof(TileTab);  // 32 tile-copy offsets (uint64)
-    static constexpr size_t SMEM_BYTES = KOFF_OFF + 32 * sizeof(uint64_t);
+    // the launch's task and its rounds' layer parameters, copied once per CTA
+    static constexpr size_t TASK_OFF = (KOFF_OFF + 32 * sizeof(uint64_t) + 15) & ~(size_t)15;
+    static constexpr size_t LAY_OFF = (TASK_OFF + sizeof(SweepTask) + 15) & ~(size_t)15;
+    static constexpr size_t SMEM_BYTES = LAY_OFF + kMaxRounds * sizeof(LayerDev);
     // V_ZPHASE: FP64 spin-expectation accumulators [kZSlots][kZQ], then the warp sums
     static constexpr size_t Z_BYTES = (size_t)kZSlots * kZQ * 8 + (size_t)(NT / 32) * (K + 1) * 4;
     static_assert(SMEM_BYTES % 8 == 0, "accumulators follow the tile tables");
@@ -282,23 +285,18 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + NB * S::BUF_BYTES);  // one barrier per buffer
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     uint64_t* koff = reinterpret_cast<uint64_t*>(smraw + S::KOFF_OFF);
+    // one task per launch (checked on the host): read from shared memory,
+    // so the per-tile and per-round fields are short-latency loads
+    const SweepTask& T = *reinterpret_cast<const SweepTask*>(smraw + S::TASK_OFF);
+    LayerDev* slay = reinterpret_cast<LayerDev*>(smraw + S::LAY_OFF);
     double* zacc = reinterpret_cast<double*>(smraw + S::SMEM_BYTES);  // kZ: [kZSlots][kZQ]
     float* zred = reinterpret_cast<float*>(smraw + S::SMEM_BYTES + (size_t)kZSlots * kZQ * 8);
     float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // kSTab: [kPairTabSmem]
     const uint32_t tid = threadIdx.x;
-    const bool zon = kZ && (tasks[0].flags & T_ZEXP);  // one task per launch
+    const bool zon = kZ && (tasks[0].flags & T_ZEXP);
     uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
     float2 X[NJ], Y[NJ];
 
-    auto find_task = [&](int64_t gt) -> int {
-        if (ntasks == 1) return 0;
-        int lo = 0, hi = ntasks - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(prefix + mid) <= gt) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-    };
     uint32_t pend = 0;   // buffers with copies in flight
     uint32_t phase = 0;  // per buffer: parity of its next completion
     // every thread: 16-byte cp.async copies of its share of the strided tile
@@ -307,7 +305,6 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     auto issue = [&](int64_t gt, int b) {
         if constexpr (TM) {
             if (tid == 0) {
-                const SweepTask& T = tasks[0];
                 const TMap tm{T.c, T.g0, T.n1, T.g1, K};
                 fence_proxy_async();  // the buffer's generic accesses before the async writes
                 mbar_expect_tx(full + b, (uint32_t)S::BUF_BYTES);
@@ -316,15 +313,12 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
             pend |= 1u << b;
             return;
         }
-        const int ti = find_task(gt);
-        const SweepTask& T = tasks[ti];
-        const int64_t tile = gt - __ldg(prefix + ti);
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
         // thread t copies elements e = 2t + 256k, k < 32: the landing map and
         // the global offset split into a per-thread part and the k part
         // (koff[k] = gofs(256 k), the same for every tile of the launch)
         const uint32_t e_t = 2u * tid;
-        const float2* src = reinterpret_cast<const float2*>(T.psi) + tm.base(tile) + tm.gofs(e_t);
+        const float2* src = reinterpret_cast<const float2*>(T.psi) + tm.base(gt) + tm.gofs(e_t);
         const uint32_t sb = smem_u32(smraw + b * S::BUF_BYTES), lt = land<P>(e_t);
 #pragma unroll
         for (int k = 0; k < 32; ++k)
@@ -339,9 +333,13 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         for (int b = 0; b < NB; ++b) mbar_init(full + b, TM ? 1 : NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (!TM && tid < 32) {  // the launch's tiles share one shape
+    {
+        const int* src = reinterpret_cast<const int*>(tasks);
+        int* dst = reinterpret_cast<int*>(smraw + S::TASK_OFF);
+        for (int i = (int)tid; i < (int)(sizeof(SweepTask) / 4); i += NT) dst[i] = __ldg(src + i);
         const SweepTask& T0 = tasks[0];
-        koff[tid] = TMap{T0.c, T0.g0, T0.n1, T0.g1, K}.gofs(256u * tid);
+        if ((int)tid < T0.nrounds) slay[tid] = T0.layers[T0.rounds[tid].layer];
+        if (!TM && tid < 32) koff[tid] = TMap{T0.c, T0.g0, T0.n1, T0.g1, K}.gofs(256u * tid);
     }
     if (zon)
         for (int i = (int)tid; i < kZSlots * kZQ; i += NT) zacc[i] = 0.0;
@@ -368,12 +366,9 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
     bool failed = false;
     int b = 0;  // buffer of the current tile
     for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x, b = (b + 1 == NB ? 0 : b + 1)) {
-        const int ti = find_task(gt);
-        const SweepTask& T = tasks[ti];
-        const int64_t tile = gt - __ldg(prefix + ti);
         const int flags = T.flags, nr = T.nrounds;
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-        const uint64_t base = tm.base(tile);
+        const uint64_t base = tm.base(gt);
         const int64_t nx = gt + (int64_t)NB * gridDim.x;
         float2* buf = reinterpret_cast<float2*>(smraw + b * S::BUF_BYTES);
         float4* buf4 = reinterpret_cast<float4*>(buf);
@@ -435,7 +430,7 @@ __global__ void __launch_bounds__(128, PairOcc<V>::value)
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {
             const SweepRound rd = T.rounds[r];
-            const LayerDev ly = T.layers[rd.layer];
+            const LayerDev ly = slay[r];
             const float2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
             // the state after the previous layer, before this layer's phase
             if (zon && rd.phase_pre && rd.layer > 0) {
@@ -513,7 +508,7 @@ template <int C, int V, bool TM>
 static cudaError_t launch_pair_tm(const SweepLaunch& L, int grid, cudaStream_t st) {
     constexpr size_t smem = pair_smem<C, V, TM>();
     if (V != V_LEAN && !L.pq) return cudaErrorInvalidValue;  // the phase needs the Q tables
-    if (TM && (!L.load || !L.load->tma || L.ntasks != 1)) return cudaErrorInvalidValue;
+    if (L.ntasks != 1 || (TM && (!L.load || !L.load->tma))) return cudaErrorInvalidValue;  // one task per launch
     const PairQ pq = L.pq ? *L.pq : PairQ{};
     PairLoad tm;
     if (L.load) tm = *L.load;

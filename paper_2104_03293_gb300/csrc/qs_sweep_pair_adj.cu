@@ -57,7 +57,10 @@ struct PairAdj {
     static constexpr size_t TILE_BYTES = (size_t)8 << K;
     static constexpr size_t TT_OFF = 3 * TILE_BYTES + 64 + (size_t)NW * NSLOT * 8;  // two TileTabs
     static constexpr size_t KOFF_OFF = TT_OFF + 2 * sizeof(TileTab);  // 16 tile-copy offsets (uint64)
-    static constexpr size_t SMEM_BYTES = KOFF_OFF + 16 * sizeof(uint64_t);
+    // the launch's task and its rounds' layer parameters, copied once per CTA
+    static constexpr size_t TASK_OFF = (KOFF_OFF + 16 * sizeof(uint64_t) + 15) & ~(size_t)15;
+    static constexpr size_t LAY_OFF = (TASK_OFF + sizeof(SweepTask) + 15) & ~(size_t)15;
+    static constexpr size_t SMEM_BYTES = LAY_OFF + kMaxRounds * sizeof(LayerDev);
     // compile-time tile bits of layout g: slot bit 0 is the pack bit
     template <int g> struct Map {
         __host__ __device__ static constexpr int slot(int b) {
@@ -262,26 +265,18 @@ __global__ void __launch_bounds__(256, 1)
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     uint64_t* koff = reinterpret_cast<uint64_t*>(smraw + S::KOFF_OFF);
     float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // [kAdjTabSmem]
+    // one task per launch (checked on the host): read from shared memory,
+    // so the per-tile and per-round fields are short-latency loads
+    const SweepTask& T = *reinterpret_cast<const SweepTask*>(smraw + S::TASK_OFF);
+    LayerDev* slay = reinterpret_cast<LayerDev*>(smraw + S::LAY_OFF);
     const uint32_t tid = threadIdx.x;
     uint32_t tpar = 0;  // parity of the CTA's tile count: which TileTab
     float2 Xp[NJ], Yp[NJ], Xl[NJ], Yl[NJ];
 
-    auto find_task = [&](int64_t gt) -> int {
-        if (ntasks == 1) return 0;
-        int lo = 0, hi = ntasks - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(prefix + mid) <= gt) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-    };
     bool pending = false;
     // every thread: 16-byte cp.async copies of its share of both strided
     // tiles, completing on the barrier (one arrival per thread)
-    auto issue = [&](int64_t gt) {
-        const int ti = find_task(gt);
-        const SweepTask& T = tasks[ti];
-        const int64_t tile = gt - __ldg(prefix + ti);
+    auto issue = [&](int64_t tile) {
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
         // thread t copies elements e = 2t + 512k, k < 16, of each array: the
         // landing map and the global offset split into a per-thread part and
@@ -307,9 +302,13 @@ __global__ void __launch_bounds__(256, 1)
         mbar_init(full, NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < 16) {  // the launch's tiles share one shape
+    {
+        const int* src = reinterpret_cast<const int*>(tasks);
+        int* dst = reinterpret_cast<int*>(smraw + S::TASK_OFF);
+        for (int i = (int)tid; i < (int)(sizeof(SweepTask) / 4); i += NT) dst[i] = __ldg(src + i);
         const SweepTask& T0 = tasks[0];
-        koff[tid] = TMap{T0.c, T0.g0, T0.n1, T0.g1, K}.gofs(512u * tid);
+        if ((int)tid < T0.nrounds) slay[tid] = T0.layers[T0.rounds[tid].layer];
+        if (tid < 16) koff[tid] = TMap{T0.c, T0.g0, T0.n1, T0.g1, K}.gofs(512u * tid);
     }
     // the table of the (first) layer whose phase this sweep un-applies
     int slayer = -1;
@@ -330,12 +329,9 @@ __global__ void __launch_bounds__(256, 1)
 
     uint32_t parity = 0;
     for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
-        const int ti = find_task(gt);
-        const SweepTask& T = tasks[ti];
-        const int64_t tile = gt - __ldg(prefix + ti);
         const int flags = T.flags, nr = T.nrounds;
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-        const uint64_t base = tm.base(tile);
+        const uint64_t base = tm.base(gt);
         const int64_t nx = gt + gridDim.x;
         // the tile's cost table (warp 0), published by the barrier after the wait
         const TileTab& tt = ttab[tpar];
@@ -389,7 +385,7 @@ __global__ void __launch_bounds__(256, 1)
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {
             const SweepRound rd = T.rounds[r];
-            const LayerDev ly = T.layers[rd.layer];
+            const LayerDev ly = slay[r];
             const float2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
             float gB = 0.f, gG = 0.f;
             if (rd.phase_pre) do_phase(ltab, ly.frame, gG, rd.layer == slayer);
@@ -430,7 +426,7 @@ __global__ void __launch_bounds__(256, 1)
             if (tid < (uint32_t)np) {
                 double s = 0.0;
                 for (int w = 0; w < NW; ++w) s += red[w * NSLOT + tid];
-                T.partials[(T.part_base + tile) * np + tid] = s;
+                T.partials[(T.part_base + gt) * np + tid] = s;
             }
             __syncthreads();
         }
@@ -451,7 +447,7 @@ static cudaError_t launch_pair_adj_cfg(const SweepLaunch& L, int grid, cudaStrea
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (!L.paq) return cudaErrorInvalidValue;  // the un-phase needs the Q tables
+    if (!L.paq || L.ntasks != 1) return cudaErrorInvalidValue;  // the un-phase's Q tables; one task per launch
     sweep_pair_adj_kernel<C><<<grid, PairAdj<C>::NT, pair_adj_smem<C>(), st>>>(L.tasks, L.tile_prefix, L.ntasks,
                                                                                 L.total_tiles, L.err, *L.paq);
     return note_launch(cudaGetLastError());

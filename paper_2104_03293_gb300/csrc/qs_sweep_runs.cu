@@ -35,7 +35,10 @@ struct RunsSweep {
     static constexpr int K = kPairK, NT = 128, NJ = 32, P = 0;
     static constexpr size_t BUF_BYTES = (size_t)8 << K;
     static constexpr size_t TT_OFF = BUF_BYTES + 64;  // two TileTabs (by tile parity)
-    static constexpr size_t SMEM_BYTES = TT_OFF + 2 * sizeof(TileTab);
+    // the launch's task and its rounds' layer parameters, copied once per CTA
+    static constexpr size_t TASK_OFF = (TT_OFF + 2 * sizeof(TileTab) + 15) & ~(size_t)15;
+    static constexpr size_t LAY_OFF = (TASK_OFF + sizeof(SweepTask) + 15) & ~(size_t)15;
+    static constexpr size_t SMEM_BYTES = LAY_OFF + kMaxRounds * sizeof(LayerDev);
     static_assert(SMEM_BYTES % 16 == 0, "the staged phase table follows the tile tables");
     static_assert(kRunBits == 8 && K == 13, "layouts of pair_runs_layout");
     template <int g> struct Map {
@@ -162,26 +165,18 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
     uint64_t* full = reinterpret_cast<uint64_t*>(smraw + S::BUF_BYTES);
     TileTab* ttab = reinterpret_cast<TileTab*>(smraw + S::TT_OFF);
     float2* stab = reinterpret_cast<float2*>(smraw + S::SMEM_BYTES);  // kPhase: [kRunsTabSmem]
+    // one task per launch (checked on the host): read from shared memory,
+    // so the per-tile and per-round fields are short-latency loads
+    const SweepTask& T = *reinterpret_cast<const SweepTask*>(smraw + S::TASK_OFF);
+    LayerDev* slay = reinterpret_cast<LayerDev*>(smraw + S::LAY_OFF);
     const uint32_t tid = threadIdx.x;
     uint32_t tpar = 0;
     float2 X[NJ], Y[NJ];
 
-    auto find_task = [&](int64_t gt) -> int {
-        if (ntasks == 1) return 0;
-        int lo = 0, hi = ntasks - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(prefix + mid) <= gt) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-    };
     bool pending = false;
     // thread 0 arrives with the byte count, every other thread plainly; warp 0
     // issues one 2 KB bulk copy per lane (32 runs)
-    auto issue = [&](int64_t gt) {
-        const int ti = find_task(gt);
-        const SweepTask& T = tasks[ti];
-        const int64_t tile = gt - __ldg(prefix + ti);
+    auto issue = [&](int64_t tile) {
         if (tid == 0) mbar_expect_tx(full, (uint32_t)S::BUF_BYTES);
         else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(full)) : "memory");
         if (tid < 32) {
@@ -200,6 +195,12 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
     if (tid == 0) {
         mbar_init(full, NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    {
+        const int* src = reinterpret_cast<const int*>(tasks);
+        int* dst = reinterpret_cast<int*>(smraw + S::TASK_OFF);
+        for (int i = (int)tid; i < (int)(sizeof(SweepTask) / 4); i += NT) dst[i] = __ldg(src + i);
+        if ((int)tid < tasks[0].nrounds) slay[tid] = tasks[0].layers[tasks[0].rounds[tid].layer];
     }
     // the table of the (first) layer whose phase this sweep applies
     int slayer = -1;
@@ -220,12 +221,9 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
 
     uint32_t parity = 0;
     for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
-        const int ti = find_task(gt);
-        const SweepTask& T = tasks[ti];
-        const int64_t tile = gt - __ldg(prefix + ti);
         const int flags = T.flags, nr = T.nrounds;
         const TMap tm{T.c, T.g0, T.n1, T.g1, K};
-        const uint64_t base = (uint64_t)tile << (kRunBits + 1);
+        const uint64_t base = (uint64_t)gt << (kRunBits + 1);
         const int64_t nx = gt + gridDim.x;
         // the tile's cost table (warp 0), published by the barrier after the wait
         const TileTab& tt = ttab[tpar];
@@ -266,7 +264,7 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
         const float2* tab = reinterpret_cast<const float2*>(T.tab);
         for (int r = 0; r < nr; ++r) {
             const SweepRound rd = T.rounds[r];
-            const LayerDev ly = T.layers[rd.layer];
+            const LayerDev ly = slay[r];
             const float2* ltab = tab + (int64_t)rd.layer * T.tab_stride;
             if (kPhase && rd.phase_pre) do_phase(ltab, ly.frame, rd.layer == slayer);
             const float w = (float)ly.w;
@@ -317,6 +315,7 @@ static cudaError_t launch_runs_cfg(const SweepLaunch& L, int grid, cudaStream_t 
         attr_set = true;
     }
     if (V != V_LEAN && !L.pq) return cudaErrorInvalidValue;  // the phase needs the Q tables
+    if (L.ntasks != 1) return cudaErrorInvalidValue;           // one task per launch
     const PairQ pq = L.pq ? *L.pq : PairQ{};
     sweep_runs_kernel<V><<<grid, RunsSweep::NT, runs_smem<V>(), st>>>(L.tasks, L.tile_prefix, L.ntasks,
                                                                       L.total_tiles, L.err, pq);
