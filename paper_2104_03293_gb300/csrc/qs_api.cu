@@ -707,6 +707,21 @@ struct CallBlob {
 // zexp: every sweep holding a layer boundary (a phase of layer k >= 1) or the
 // readout also records <Z_q> of the state after layer k - 1 (resp. p - 1)
 // into per-CTA records, reduced after the sweep into h->zout[layer][n].
+// Kernel of a forward sweep: the variant (sweep_variant) and the packed-pair
+// kernel (pair_choice; 0 = the generic sweep kernel).  The first and the
+// readout sweep of the run-structured shape A run on its packed-pair kernel
+// (V_RUNS_GEN, V_RUNS_READ) when they do nothing else.
+static void forward_kernel(qs_handle h, const Shape& sh, const PlanSweep& s, int& variant, int& pairc) {
+    variant = sweep_variant(s.flags, s.nr, s.r);
+    pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, variant);
+    const int fl = s.flags & (T_GEN | T_READOUT | T_WRITE_LAM | T_ADJOINT | T_ZEXP | T_SU2);
+    if (variant == V_FULL && (fl == T_GEN || fl == T_READOUT) &&
+        pair_choice(h->dtype, 0, sh.kind, sh.c, V_PHASE) == 1) {
+        variant = fl == T_GEN ? V_RUNS_GEN : V_RUNS_READ;
+        pairc = 1;
+    }
+}
+
 static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int objective, bool zexp = false,
                      const double* su2 = nullptr) {
     Instance& I = h->inst;
@@ -750,8 +765,8 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     for (auto& s : fwd) {
         SweepTask t = make_task(h, shf[s.shape], s, 0, s.shape, h->lam, lf, h->tab_f.ptr, p, dpart, objective);
         const Shape& sh = shf[s.shape];
-        const int variant = sweep_variant(s.flags, s.nr, s.r);
-        const int pc = pair_choice(h->dtype, 0, sh.kind, sh.c, variant);
+        int variant = 0, pc = 0;
+        forward_kernel(h, sh, s, variant, pc);
         if (pc)
             for (int g = 0; g < kMaxLayouts; ++g) t.cprog[g] = I.prog(I.prog_pair[s.shape][g < 2 ? g : 0]);
         t.zpart = dzp;
@@ -804,10 +819,10 @@ static int run_tiled(qs_handle h, int p, bool from_plus, int mode_grad, int obje
     }
     for (size_t i = 0; i < fwd.size(); ++i) {
         const Shape& sh = shf[fwd[i].shape];
-        SweepLaunch L{kernel_kind(sh), sweep_variant(fwd[i].flags, fwd[i].nr, fwd[i].r), 0, h->dtype, 1, sh.ntiles,
+        SweepLaunch L{kernel_kind(sh), 0, 0, h->dtype, 1, sh.ntiles,
                       reinterpret_cast<const SweepTask*>(dblob + fwd_off[i]),
                       reinterpret_cast<const int64_t*>(dblob + fwd_pre[i]), derr};
-        L.pairc = pair_choice(h->dtype, 0, sh.kind, sh.c, L.variant);
+        forward_kernel(h, sh, fwd[i], L.variant, L.pairc);
         L.pq = &I.pair_q[fwd[i].shape];
         L.cluster = h->pair_cluster;
         PairLoad pl;

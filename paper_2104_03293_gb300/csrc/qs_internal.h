@@ -67,6 +67,10 @@ constexpr int kZSlots = kMaxRounds + 1;  // records per CTA
 // kernel; sweep_kernel runs ZPHASE sweeps as ZFULL).  SU2 is FULL with
 // general per-qubit 2 x 2 unitaries in place of the x rotations.
 enum : int { V_FULL = 0, V_PHASE = 1, V_LEAN = 2, V_ZFULL = 3, V_ZPHASE = 4, V_SU2 = 5 };
+// Run-structured shape A only (sweep_runs_kernel): the first sweep of an
+// evolve (|+> generated, the first layer's phase and rotations; no load)
+// and the last one (rotations, then E, P_ground and the norm per tile).
+enum : int { V_RUNS_GEN = 6, V_RUNS_READ = 7 };
 
 struct SweepRound {
     int layer;       // index into the per-layer parameter array

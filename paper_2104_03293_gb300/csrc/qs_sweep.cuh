@@ -360,6 +360,55 @@ __device__ __forceinline__ void pair_phase(float2 (&X)[32], float2 (&Y)[32], con
     }
 }
 
+// Readout of a thread's 64 amplitudes held as 32 packed pairs (layout Map,
+// as pair_phase): with the slot costs walked as in pair_phase, accumulates
+// E += |psi|^2 C, P += |psi|^2 on the minimal cost (table index gidx) and
+// N += |psi|^2, in float.
+template <class Map, int NTB>
+__device__ __forceinline__ void pair_readout(const float2 (&X)[32], const float2 (&Y)[32],
+                                             const int32_t* __restrict__ lp, const TileTab& tt, uint32_t tid,
+                                             int frame, int cost_lo, int gidx, const int32_t (&q)[64], float& E,
+                                             float& P, float& N) {
+    const int sg = frame ? -1 : 1;
+    const int4* tr = reinterpret_cast<const int4*>(lp + 64) + 2 * tid;
+    const int4 ta = __ldg(tr), tb4 = __ldg(tr + 1);
+    const int hrt[6] = {ta.y, ta.z, ta.w, tb4.x, tb4.y, tb4.z};
+    int base = sg * tt.kf + tt.kc + ta.x - cost_lo;
+    static_for<0, NTB>([&](auto jc) {
+        constexpr int t = decltype(jc)::value;
+        constexpr int tb = Map::thr(t);
+        const int v = sg * tt.H[tb] + tt.D[tb];
+        base += ((tid >> t) & 1u) ? -v : v;
+    });
+    int f2[6];
+    static_for<0, 6>([&](auto bc) {
+        constexpr int bb = decltype(bc)::value;
+        constexpr int tb = Map::slot(bb);
+        const int fb = sg * tt.H[tb] + tt.D[tb] + hrt[bb];
+        base += fb;
+        f2[bb] = 2 * fb;
+    });
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        int run = base - ((ch & 1) ? f2[4] : 0) - ((ch & 2) ? f2[5] : 0);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int gc = i ^ (i >> 1);
+            if (i > 0) {
+                const int bb = __ffs(i) - 1;
+                run += ((gc >> bb) & 1) ? -f2[bb] : f2[bb];
+            }
+            const int m = (ch << 4) | gc, j = m >> 1;
+            const int ix = run + q[m];
+            const float re = (m & 1) ? X[j].y : X[j].x, im = (m & 1) ? Y[j].y : Y[j].x;
+            const float w2 = fmaf(re, re, im * im);
+            E = fmaf(w2, (float)(ix + cost_lo), E);
+            N += w2;
+            if (ix == gidx) P += w2;
+        }
+    }
+}
+
 // Warp-level sum, lane 0 stores into red[warp * nslots + slot].
 __device__ __forceinline__ void warp_sum_to(double v, double* red, int slot, int nslots) {
 #pragma unroll

@@ -38,7 +38,8 @@ struct RunsSweep {
     // the launch's task and its rounds' layer parameters, copied once per CTA
     static constexpr size_t TASK_OFF = (TT_OFF + 2 * sizeof(TileTab) + 15) & ~(size_t)15;
     static constexpr size_t LAY_OFF = (TASK_OFF + sizeof(SweepTask) + 15) & ~(size_t)15;
-    static constexpr size_t SMEM_BYTES = LAY_OFF + kMaxRounds * sizeof(LayerDev);
+    static constexpr size_t RED_OFF = LAY_OFF + kMaxRounds * sizeof(LayerDev);  // readout warp sums [4][3]
+    static constexpr size_t SMEM_BYTES = RED_OFF + (NT / 32) * 3 * sizeof(double);
     static_assert(SMEM_BYTES % 16 == 0, "the staged phase table follows the tile tables");
     static_assert(kRunBits == 8 && K == 13, "layouts of pair_runs_layout");
     template <int g> struct Map {
@@ -158,7 +159,10 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
                       int64_t total, int* __restrict__ err, const __grid_constant__ PairQ pq) {
     using S = RunsSweep;
     constexpr int K = S::K, NT = S::NT, NJ = S::NJ;
-    constexpr bool kPhase = V == V_PHASE;
+    // V_RUNS_GEN: |+> generated in registers, no load; V_RUNS_READ: E, P and
+    // the norm of the tile after its rounds, as per-tile partials
+    constexpr bool kGen = V == V_RUNS_GEN, kRead = V == V_RUNS_READ;
+    constexpr bool kPhase = V != V_LEAN;
     extern __shared__ __align__(128) unsigned char smraw[];
     float2* buf = reinterpret_cast<float2*>(smraw);
     float4* buf4 = reinterpret_cast<float4*>(smraw);
@@ -169,6 +173,7 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
     // so the per-tile and per-round fields are short-latency loads
     const SweepTask& T = *reinterpret_cast<const SweepTask*>(smraw + S::TASK_OFF);
     LayerDev* slay = reinterpret_cast<LayerDev*>(smraw + S::LAY_OFF);
+    double* red = reinterpret_cast<double*>(smraw + S::RED_OFF);  // kRead: warp sums [NT / 32][3]
     const uint32_t tid = threadIdx.x;
     uint32_t tpar = 0;
     float2 X[NJ], Y[NJ];
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
         }
     }
     __syncthreads();
-    if ((int64_t)blockIdx.x < total) issue(blockIdx.x);
+    if (!kGen && (int64_t)blockIdx.x < total) issue(blockIdx.x);
 
     uint32_t parity = 0;
     for (int64_t gt = blockIdx.x; gt < total; gt += gridDim.x) {
@@ -229,21 +234,32 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
         const TileTab& tt = ttab[tpar];
         if (kPhase && tid < 32) tile_tab_fill(&ttab[tpar], T.tprog, base, tid);
         tpar ^= 1u;
-        const int ok = mbar_wait_bounded(full, parity) ? 1 : 0;
-        if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
-            if (tid == 0) atomicExch(err, 1);
-            break;
+        if constexpr (kGen) {
+            // |+>^n: every amplitude 2^{-n/2}, real
+            __syncthreads();  // the tile table is published
+            const float a0 = (float)T.amp0;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                X[j] = make_float2(a0, a0);
+                Y[j] = make_float2(0.f, 0.f);
+            }
+        } else {
+            const int ok = mbar_wait_bounded(full, parity) ? 1 : 0;
+            if (!__syncthreads_and(ok)) {  // the copies stay pending on this phase
+                if (tid == 0) atomicExch(err, 1);
+                break;
+            }
+            parity ^= 1u;
+            pending = false;
+            S::lds_dense0(buf, X, Y, tid);
+            __syncthreads();  // dense reads done before the swizzled writes
         }
-        parity ^= 1u;
-        pending = false;
-        S::lds_dense0(buf, X, Y, tid);
-        __syncthreads();  // dense reads done before the swizzled writes
         // each round moves once to the other layout; an odd count moves back
         const int ntr = nr + (nr & 1);
         int done_tr = 0, cur = 0;
         auto release = [&]() {
             __syncthreads();
-            if (nx < total) issue(nx);
+            if (!kGen && nx < total) issue(nx);
         };
         if (ntr == 0) release();
         auto to_layout = [&](int g) {
@@ -281,6 +297,14 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
         }
         to_layout(0);
 
+        if (kRead && (flags & T_READOUT)) {
+            float E = 0.f, Pg = 0.f, N = 0.f;
+            pair_readout<typename S::template Map<0>, 7>(X, Y, T.cprog[0], tt, tid, T.layers[T.end_layer].frame,
+                                                         T.cost_lo, T.gidx, pq.q[0], E, Pg, N);
+            warp_sum_to((double)E, red, 0, 3);
+            warp_sum_to((double)Pg, red, 1, 3);
+            warp_sum_to((double)N, red, 2, 3);
+        }
         if (flags & T_STORE) {
             // layout 0: slot bits are run bits 6, 7 (in the run) and tile bits
             // 8..10 (global bits g0..g0 + 2); lanes on run bits 1..5
@@ -293,6 +317,15 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
                 dst[off >> 1] = make_float4(X[j].x, Y[j].x, X[j].y, Y[j].y);
             }
         }
+        if (kRead && T.np > 0) {  // the tile's partials: E, P, norm
+            __syncthreads();
+            if (tid < (uint32_t)T.np) {
+                double sum = 0.0;
+                for (int w = 0; w < NT / 32; ++w) sum += red[w * 3 + tid];
+                T.partials[(T.part_base + gt) * T.np + tid] = sum;
+            }
+            __syncthreads();
+        }
     }
     // before the shared memory goes away: wait (bounded) for copies in flight;
     // a drain that gives up is reported with the sticky status 2
@@ -302,7 +335,7 @@ __global__ void __launch_bounds__(128, V == V_PHASE ? QS_PHASE_OCC : 3)
 
 template <int V>
 static size_t runs_smem() {
-    return RunsSweep::SMEM_BYTES + (V == V_PHASE ? (size_t)kRunsTabSmem * sizeof(float2) : 0);
+    return RunsSweep::SMEM_BYTES + (V != V_LEAN ? (size_t)kRunsTabSmem * sizeof(float2) : 0);
 }
 
 template <int V>
@@ -314,7 +347,7 @@ static cudaError_t launch_runs_cfg(const SweepLaunch& L, int grid, cudaStream_t 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (V != V_LEAN && !L.pq) return cudaErrorInvalidValue;  // the phase needs the Q tables
+    if (V != V_LEAN && !L.pq) return cudaErrorInvalidValue;  // the phase and the readout need the Q tables
     if (L.ntasks != 1) return cudaErrorInvalidValue;           // one task per launch
     const PairQ pq = L.pq ? *L.pq : PairQ{};
     sweep_runs_kernel<V><<<grid, RunsSweep::NT, runs_smem<V>(), st>>>(L.tasks, L.tile_prefix, L.ntasks,
@@ -325,6 +358,8 @@ static cudaError_t launch_runs_cfg(const SweepLaunch& L, int grid, cudaStream_t 
 cudaError_t launch_sweep_runs(const SweepLaunch& L, int grid, cudaStream_t st) {
     if (L.variant == V_PHASE) return launch_runs_cfg<V_PHASE>(L, grid, st);
     if (L.variant == V_LEAN) return launch_runs_cfg<V_LEAN>(L, grid, st);
+    if (L.variant == V_RUNS_GEN) return launch_runs_cfg<V_RUNS_GEN>(L, grid, st);
+    if (L.variant == V_RUNS_READ) return launch_runs_cfg<V_RUNS_READ>(L, grid, st);
     return cudaErrorInvalidValue;
 }
 
