@@ -227,3 +227,29 @@ def test_pair_landing_reads_conflict_free(C, adjoint):
                 for w0 in range(0, 1 << ntb, 16):
                     slots = {lf(et[w0 + l] | es | (h << P), P) % 16 for l in range(16)}
                     assert len(slots) == 16, (C, adjoint, g, j, h, w0)
+
+
+def test_gray_slot_walk_visits_every_slot_with_its_cost():
+    """The packed-pair phase and readout walk a thread's 64 slots in four
+    Gray-code chains of 16 (slot bits 4 and 5 fixed per chain), adding or
+    subtracting one doubled slot term per step: every slot is visited once
+    and its running value equals base - sum of 2 fb[b] over its set bits."""
+    import random
+    rng = random.Random(3)
+    for _ in range(20):
+        fb = [rng.randint(-9, 9) for _ in range(6)]
+        base = rng.randint(-50, 50)
+        f2 = [2 * x for x in fb]
+        seen = {}
+        for ch in range(4):
+            run = base - (f2[4] if ch & 1 else 0) - (f2[5] if ch & 2 else 0)
+            for i in range(16):
+                gc = i ^ (i >> 1)
+                if i > 0:
+                    bb = (i & -i).bit_length() - 1
+                    run += -f2[bb] if (gc >> bb) & 1 else f2[bb]
+                m = (ch << 4) | gc
+                seen[m] = run
+        assert sorted(seen) == list(range(64))
+        for m, v in seen.items():
+            assert v == base - sum(f2[b] for b in range(6) if (m >> b) & 1)
